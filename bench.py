@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused D2Q9 MRT pseudopotential update on GB300.
+
+Workload (one bench "step"): a 2048 x 2048 periodic lattice holding a Carnahan-Starling
+droplet (a = 1, b = 4, R = 1, T = 0.8 T_c, G = -1, kappa = 0.6, nu = 0.1, radius 200,
+tanh width 2, Maxwell densities), advanced by INNER = 100 time steps through lb_step
+followed by one FP64 diagnostics reduction (lb_reduce: mass, momentum, max |u|).
+Populations are FP32 (two buffers of 151 MB each, larger than the 129 MB L2).
+
+Printed: one JSON line (rank 0). `value` = MLUPS over all ranks (device-timed, inputs
+resident); `e2e` = the same through the C ABI with host buffers (populations in from
+pinned host memory, density field out to pinned host memory, every step);
+`roofline` = the fused kernel's algorithmic bytes per launch / its live CUDA-event
+duration against the measured HBM copy bandwidth; `fp64` = the same workload in FP64;
+`cpu_baseline` = the FP64 numpy oracle on one host core over a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU (torchrun): every rank advances its own replica lattice (the path does not
+shard); `value` = total lattice updates of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64 on GB300; batched droplets/sec at σ err ≤1%"
+NX, NY, INNER = 2048, 2048, 100
+WORKLOAD = ("D2Q9 MRT pseudopotential droplet 2048x2048 periodic, Carnahan-Starling T=0.8Tc, "
+            "G=-1, kappa=0.6, nu=0.1, R=200; 100 LB steps + 1 FP64 reduction per bench step")
+ALG_BYTES_PER_SITE = {"fp32": 72, "fp64": 144}   # 9 populations read + 9 written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--inner", type=int, default=INNER)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("lb_device.cuh", "lb_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1306_6445_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec: str):
+    """DRAM bytes per fused-step launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"fused_step_{prec}_2048sq.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_b) or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def droplet_setup(lbm, inputs, nx, ny):
+    eos = lbm.cs_eos(0.8)
+    rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
+    rates = lbm.RateParams.from_viscosity(0.1)
+    rho = inputs.droplet_density(nx, ny, 200.0 * min(nx, ny) / 2048.0, rl, rv)
+    return eos, rates, rho
+
+
+# --------------------------------------------------------------------------------------
+# native arm
+# --------------------------------------------------------------------------------------
+
+def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist):
+    eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
+    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec)
+    lat.set_rho_u(rho)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lat.step(inner)
+        lat.reduce()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        lat.step(inner)
+        ev[k][1].record(stream)
+        lat.reduce()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = steps * (inner * lbm.lb_kernels_per_step(lat.ctx) + 3)
+    lat.close()
+    return total_ms, step_kernel_ms / (steps * inner), launches
+
+
+def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
+    """Through the C ABI with host buffers: each step copies the populations in from pinned
+    host memory (lb_set_populations), runs `inner` steps and reads the density field back
+    into pinned host memory (lb_get_rho)."""
+    eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
+    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec="fp32")
+    lat.set_rho_u(rho)
+    f_host = torch.empty((9, ny, nx), dtype=torch.float32, pin_memory=True)
+    import numpy as np
+    f_host.numpy()[...] = lat.populations()
+    rho_host = torch.empty((ny, nx), dtype=torch.float64, pin_memory=True)
+    rho_np = rho_host.numpy()
+    bi, bo = f_host.numel() * 4, rho_host.numel() * 8
+
+    def one():
+        lbm.lb_set_populations(lat.ctx, f_host.data_ptr(), bi)
+        lbm.lb_step(lat.ctx, inner)
+        lbm.lb_get_rho(lat.ctx, rho_np)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    lat.close()
+    assert np.isfinite(rho_np).all()
+    return el, bi, bo
+
+
+def cpu_baseline(nx, ny, budget_s=20.0):
+    """The FP64 numpy oracle, single thread, on the same droplet lattice: as many whole
+    steps as fit in ~budget_s (at least one). Runs in a child process so the BLAS thread
+    count can be pinned to one."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import eos as OE, lattice as OL
+from paper_1306_6445_gb300 import inputs
+nx, ny, budget = %d, %d, %f
+eos = OE.cs_eos(0.8)
+rv, rl, _ = OE.maxwell(eos, -1.0)
+rho = inputs.droplet_density(nx, ny, 200.0 * min(nx, ny) / 2048.0, rl, rv)
+f = OL.equilibrium(rho, 0 * rho, 0 * rho)
+p = OL.Params(eos=eos, G=-1.0, kappa=0.6, rates=OL.Rates.from_viscosity(0.1))
+t = time.perf_counter(); n = 0
+while True:
+    f = OL.step(f, p); n += 1
+    if time.perf_counter() - t > budget: break
+el = time.perf_counter() - t
+print(json.dumps({"steps": n, "seconds": el, "mlups": nx * ny * n / el / 1e6}))
+""" % (ROOT, nx, ny, budget_s)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": "MLUPS", "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["mlups"], 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} FP64 steps of the full {nx}x{ny} lattice "
+                      f"({d['seconds']:.1f} s, numpy, 1 thread)"}
+
+
+def native(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1306_6445_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1306_6445_gb300 import inputs, lbm
+
+    nx, ny, inner, K, W = args.nx, args.ny, args.inner, args.steps, args.warmup
+    sites = nx * ny
+    with ClockSampler(local) as clocks:
+        total_ms, kern_ms, launches = time_precision(lbm, torch, inputs, "fp32", nx, ny, inner,
+                                                     K, W, dist)
+    t = torch.tensor([total_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * sites * inner * K / (max_ms * 1e-3) / 1e6
+
+    hbm, peak_src = measured_peaks()
+    alg = ALG_BYTES_PER_SITE["fp32"] * sites
+    achieved = alg / (kern_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("fp32")
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "kernel": "k_fused_step<float>", "alg_bytes_per_launch": alg,
+            "kernel_ms": round(kern_ms, 5), "peak_source": f"{peak_src} (copy bandwidth)"}
+
+    # FP64 leg
+    fk = max(args.fp64_steps, 1)
+    f_total, f_kern, _ = time_precision(lbm, torch, inputs, "fp64", nx, ny, inner, fk, 1, dist)
+    alg64 = ALG_BYTES_PER_SITE["fp64"] * sites
+    fp64 = {"value": round(sites * inner * fk / (f_total * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "kernel_ms": round(f_kern, 5),
+            "hbm_frac": round(alg64 / (f_kern * 1e-3) / 1e9 / hbm, 4),
+            "note": "FP64 update is bound by FP64 ALU throughput on GB300, not HBM"}
+
+    e2e = None
+    if not args.no_e2e:
+        el, bi, bo = time_e2e(lbm, torch, inputs, nx, ny, inner, K, min(W, 2))
+        e2e = {"value": round(world * sites * inner * K / el / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    if rank == 0:
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(nx, ny)
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": round(max_ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "lb_steps_per_step": inner,
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"},
+            "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# --------------------------------------------------------------------------------------
+
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # one host thread for numpy's BLAS: set before numpy is first imported
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    from oracle import eos as OE
+    from oracle import lattice as OL
+    from paper_1306_6445_gb300 import inputs
+
+    # bounded sample of the workload: a 2048 x 128 band of the droplet lattice, periodic,
+    # one LB step per bench step (the oracle needs ~1 s per 3 M site updates)
+    nx, ny = args.nx, min(args.ny, 128)
+    eos = OE.cs_eos(0.8)
+    rv, rl, _ = OE.maxwell(eos, -1.0)
+    rho_full = inputs.droplet_density(args.nx, args.ny, 200.0 * min(args.nx, args.ny) / 2048.0,
+                                      rl, rv)
+    y0 = args.ny // 2 - ny // 2
+    rho = rho_full[y0:y0 + ny]
+    f = OL.equilibrium(rho, 0 * rho, 0 * rho)
+    p = OL.Params(eos=eos, G=-1.0, kappa=0.6, rates=OL.Rates.from_viscosity(0.1))
+    for _ in range(args.warmup):
+        f = OL.step(f, p)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f = OL.step(f, p)
+    el = time.perf_counter() - t
+    v = nx * ny * args.steps / el / 1e6
+    sample = f"{args.steps} FP64 steps of a {nx}x{ny} band of the droplet lattice (numpy, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": args.nx, "ny": args.ny,
+                   "sample": f"{nx}x{ny} band, 1 LB step per bench step"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

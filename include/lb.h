@@ -1,0 +1,173 @@
+/*
+ * lb.h - C ABI of the GB300 (sm_103a) library for the tunable-surface-tension
+ * pseudopotential lattice Boltzmann method of Li & Luo (arXiv 1306.6445).
+ *
+ * One context = one D2Q9 lattice of nx * ny sites on one GPU. Each call of
+ * lb_step advances it by whole time steps of the MRT pseudopotential update:
+ *   rho = sum f, psi(rho)                          (Sec. II, Eq. 6 and text after Eq. 7)
+ *   F = -G psi(x) sum_a w_a psi(x + e_a) e_a      (Eq. 7, w(1) = 1/3, w(2) = 1/12)
+ *   Q = kappa G/2 psi(x) sum_a w_a [psi(x + e_a) - psi(x)] e_a e_a     (Eq. 19)
+ *   rho v = sum e f + F/2                          (Eq. 6)
+ *   m* = m - Lambda (m - m_eq) + (I - Lambda/2) S + C                  (Eq. 17)
+ *     with m_eq of Eq. 3, S of Eq. 5 whose S_1 is Eq. 8, C of Eq. 18
+ *   f* = M^-1 m*, then streaming f_a(x + e_a, t + 1) = f*_a(x, t)      (Eq. 4)
+ * Lattice units c = delta_x = delta_t = 1, c_s^2 = 1/3.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Velocities e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ * - Host field arrays are row-major [y][x] (x fastest), nx * ny doubles, owned by
+ *   the caller. Host population arrays are [alpha][y][x], 9 * ny * nx elements of
+ *   the context's storage type (double for LB_FP64, float for LB_FP32).
+ * - Populations are stored on the device as 9 planes of ny rows of `pitch`
+ *   elements (pitch = lb_pitch(nx, prec) >= nx, a multiple of 32 elements).
+ * - Every function returns an lb_status; nothing throws across the ABI. After
+ *   LB_ENONFINITE, LB_EDOMAIN or LB_ETIMEOUT the context is poisoned: every later
+ *   call except lb_free / lb_last_error / lb_status_of returns that code again.
+ * - Calls on one context are not thread-safe. Work is queued on the context's
+ *   stream; calls that return data to the host synchronise that stream.
+ */
+#ifndef PAPER_1306_6445_GB300_LB_H
+#define PAPER_1306_6445_GB300_LB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,      /* bad argument (sizes, rates, kappa, buffer size, ...) */
+    LB_ENOMEM = 2,      /* device or host allocation failed */
+    LB_ECUDA = 3,       /* a CUDA runtime call failed (message in lb_last_error) */
+    LB_ENONFINITE = 4,  /* a reduction found a non-finite mass or momentum */
+    LB_EDOMAIN = 5,     /* psi^2 < 0 or rho <= 0 at some site: EOS left its real branch */
+    LB_ETIMEOUT = 6     /* a bounded device-side wait gave up */
+} lb_status;
+
+typedef enum { LB_EOS_CS = 0, LB_EOS_EXP = 1, LB_EOS_PIECEWISE = 2 } lb_eos_kind;
+typedef enum { LB_FP64 = 0, LB_FP32 = 1 } lb_prec;
+typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS_Y = 1 } lb_bc;
+
+/* Equation of state / pseudopotential (Sec. II; Eq. 23).
+ *  LB_EOS_CS:        p = rho R T (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2, eta = b rho/4;
+ *                    psi = sqrt(2 (p - rho/3) / G)
+ *  LB_EOS_EXP:       psi = psi0 exp(-rho0 / rho)
+ *  LB_EOS_PIECEWISE: p of Eq. 23 with theta_v, theta_m, theta_l, rho1, rho2;
+ *                    psi = sqrt(2 (p - rho/3) / G)                                   */
+typedef struct {
+    int kind;                              /* lb_eos_kind */
+    double a, b, R, T;                     /* Carnahan-Starling */
+    double psi0, rho0;                     /* exponential potential */
+    double theta_v, theta_m, theta_l, rho1, rho2;  /* Eq. 23 */
+} lb_eos;
+
+/* Relaxation rates s = 1/tau of Lambda = diag(s_rho, s_e, s_zeta, s_j, s_q, s_j, s_q, s_v, s_v)
+ * (Sec. II, text after Eq. 1). Each must lie in (0, 2). */
+typedef struct {
+    double s_rho, s_e, s_zeta, s_j, s_q, s_v;
+} lb_rates;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Row pitch (elements) of the device population planes for a lattice of width nx. */
+size_t lb_pitch(int nx, int prec);
+
+/* Bytes of ONE device population buffer: 9 * ny * lb_pitch(nx, prec) * element size. */
+size_t lb_buffer_bytes(int nx, int ny, int prec);
+
+/* Create a context and allocate its two device population buffers (ping-pong).
+ *  nx, ny       lattice size, each >= 3.
+ *  eos, G       pseudopotential and interaction strength of Eq. 7 (G != 0 for the
+ *               EOS-based potentials, which divide by G).
+ *  kappa        surface-tension parameter of Eq. 19, in [0, 1).
+ *  sigma_force  the constant sigma of Eq. 8 (>= 0; 0 gives the forcing of Eq. 5).
+ *               When it is non-zero the paper requires s_zeta == s_e (text after Eq. 8).
+ *  rates        relaxation rates, each in (0, 2).
+ *  prec         LB_FP64 or LB_FP32 (storage and arithmetic type of the update).
+ *  bc           LB_BC_PERIODIC, or LB_BC_WALLS_Y: periodic in x, no-slip walls below
+ *               row 0 and above row ny-1 (half-way bounce-back; psi of the adjacent
+ *               fluid row is used at the wall, Sec. V.B names no scheme).
+ *  stream       a cudaStream_t to queue work on, or NULL for the legacy default stream.
+ * The populations are left uninitialised: call lb_set_rho_u or lb_set_populations.
+ * Errors: LB_EINVAL for any argument outside the ranges above, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_init(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
+                  double sigma_force, const lb_rates *rates, int prec, int bc, void *stream);
+
+/* As lb_init, but the two device population buffers belong to the caller (for example
+ * memory from a tensor library). Each must hold lb_buffer_bytes(nx, ny, prec) bytes,
+ * be 256-byte aligned and stay valid until lb_free. The library never frees them.
+ * Errors: as lb_init, plus LB_EINVAL for NULL or misaligned buffers. */
+lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
+                     double sigma_force, const lb_rates *rates, int prec, int bc, void *stream,
+                     void *f_a, void *f_b);
+
+/* f = f_eq(rho, u) = M^-1 m_eq(rho, u) of Eq. 3 at every site (the initial state).
+ * rho, ux, uy: host arrays of nx*ny doubles, [y][x]. The step counter is reset to 0.
+ * Synchronises the stream. Errors: LB_EINVAL (NULL), LB_EDOMAIN if psi(rho) is not real
+ * at some site (rho <= 0, or (p_EOS - rho/3)/G < 0), LB_ECUDA. */
+lb_status lb_set_rho_u(lb_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* Advance n >= 0 time steps (Eqs. 4-8, 17-19). Queued on the stream; returns without
+ * waiting. A psi-domain violation found on the device is reported by the next call
+ * that synchronises (lb_sync, lb_get_*, lb_reduce) as LB_EDOMAIN. */
+lb_status lb_step(lb_ctx *ctx, int n);
+
+/* Wait for queued work and report device-side errors (LB_EDOMAIN, LB_ECUDA). */
+lb_status lb_sync(lb_ctx *ctx);
+
+/* Density rho = sum_a f_a (Eq. 6) into a host array of nx*ny doubles. Synchronises. */
+lb_status lb_get_rho(lb_ctx *ctx, double *rho);
+
+/* Velocity v = (sum_a e_a f_a + F/2) / rho (Eq. 6, with F of Eq. 7) into two host arrays
+ * of nx*ny doubles. Synchronises. */
+lb_status lb_get_u(lb_ctx *ctx, double *ux, double *uy);
+
+/* Copy the current populations to / from a packed host array [alpha][y][x] of
+ * 9*ny*nx elements of the storage type; `bytes` must equal that size exactly.
+ * lb_set_populations resets nothing else (the step counter is kept). Both synchronise.
+ * Errors: LB_EINVAL on a size mismatch or NULL, LB_ECUDA. */
+lb_status lb_get_populations(lb_ctx *ctx, void *dst, size_t bytes);
+lb_status lb_set_populations(lb_ctx *ctx, const void *src, size_t bytes);
+
+/* Global diagnostics in FP64 with a fixed reduction order (bit-reproducible):
+ * out[0] = sum rho, out[1] = sum rho v_x, out[2] = sum rho v_y (v of Eq. 6),
+ * out[3] = max |v|. Synchronises. LB_ENONFINITE (and poisoning) if any is not finite. */
+lb_status lb_reduce(lb_ctx *ctx, double out[4]);
+
+/* Number of time steps taken since lb_set_rho_u. */
+long long lb_steps_done(const lb_ctx *ctx);
+
+/* Number of kernel launches one lb_step(ctx, 1) queues (for launch accounting). */
+int lb_kernels_per_step(const lb_ctx *ctx);
+
+/* Last error message of the context (static string "no context" for NULL). */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Sticky status of the context (LB_OK unless poisoned). */
+lb_status lb_status_of(const lb_ctx *ctx);
+
+/* Release the context and the device memory the library allocated. NULL is a no-op. */
+void lb_free(lb_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Host-side thermodynamic set-up helpers (no GPU work). They give the Carnahan-
+ * Starling critical point and the Maxwell coexistence densities used to build
+ * initial droplets (Sec. II; the Maxwell rule is equal area in 1/rho).
+ * --------------------------------------------------------------------------------- */
+
+/* Critical temperature and density of the Carnahan-Starling EOS with a, b, R.
+ * Errors: LB_EINVAL for non-positive a, b or R. */
+lb_status lb_cs_critical(double a, double b, double R, double *Tc, double *rhoc);
+
+/* Maxwell coexistence densities and pressure of `eos` (with interaction strength G for
+ * the exponential potential, whose pressure is rho/3 + G psi^2/2).
+ * Errors: LB_EINVAL when the EOS has no van der Waals loop or the solve fails. */
+lb_status lb_maxwell(const lb_eos *eos, double G, double *rho_v, double *rho_l, double *p_b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1306_6445_GB300_LB_H */

@@ -1,0 +1,378 @@
+// C ABI of the library (declared in include/lb.h): context management, argument
+// validation, device buffers and the host side of every call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lb_internal.h"
+
+using lbm::Consts;
+using lbm::Geom;
+
+struct lb_ctx {
+    Geom geom{};
+    Consts consts{};
+    int prec = LB_FP64;
+    size_t elem = 8;
+    cudaStream_t stream = nullptr;
+    void *f[2] = {nullptr, nullptr};
+    bool own_f = false;
+    int cur = 0;                 // index of the buffer holding the current populations
+    int *d_err = nullptr;        // device error bits
+    double *d_psi = nullptr;     // diagnostics: psi field (nx*ny), allocated on first use
+    double *d_field = nullptr;   // diagnostics: one nx*ny double field
+    double *d_partials = nullptr;
+    double *d_out4 = nullptr;
+    double *d_host_in = nullptr; // 3*nx*ny staging for lb_set_rho_u
+    lbm::StepLaunch launch{};
+    long long steps = 0;
+    lb_status sticky = LB_OK;
+    std::string msg;
+};
+
+namespace {
+
+const char *kNoCtx = "no context";
+
+lb_status fail(lb_ctx *c, lb_status s, const std::string &m) {
+    if (c) c->msg = m;
+    return s;
+}
+
+lb_status poison(lb_ctx *c, lb_status s, const std::string &m) {
+    c->sticky = s;
+    c->msg = m;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (c) c->msg = m;
+    return LB_ECUDA;
+}
+
+#define LB_CUDA(ctx, call)                                        \
+    do {                                                          \
+        cudaError_t e__ = (call);                                 \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call); \
+    } while (0)
+
+size_t elem_size(int prec) { return prec == LB_FP32 ? 4 : 8; }
+
+bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
+
+lb_status validate(int nx, int ny, const lb_eos *eos, double G, double kappa, double sigma,
+                   const lb_rates *r, int prec, int bc, std::string &why) {
+    if (nx < 3 || ny < 3) { why = "nx and ny must be >= 3"; return LB_EINVAL; }
+    if ((long long)nx * ny > (1LL << 31) - 1) { why = "lattice too large"; return LB_EINVAL; }
+    if (!eos || !r) { why = "eos and rates must not be NULL"; return LB_EINVAL; }
+    if (prec != LB_FP32 && prec != LB_FP64) { why = "prec must be LB_FP64 or LB_FP32"; return LB_EINVAL; }
+    if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y) { why = "bad boundary kind"; return LB_EINVAL; }
+    if (!(rate_ok(r->s_rho) && rate_ok(r->s_e) && rate_ok(r->s_zeta) && rate_ok(r->s_j) &&
+          rate_ok(r->s_q) && rate_ok(r->s_v))) {
+        why = "relaxation rates must lie in (0, 2) (tau > 1/2)";
+        return LB_EINVAL;
+    }
+    if (!(std::isfinite(kappa) && kappa >= 0.0 && kappa < 1.0)) { why = "kappa must be in [0, 1)"; return LB_EINVAL; }
+    if (!(std::isfinite(sigma) && sigma >= 0.0)) { why = "sigma_force must be >= 0"; return LB_EINVAL; }
+    if (sigma != 0.0 && r->s_zeta != r->s_e) {
+        why = "Eq. 8 requires tau_zeta == tau_e when sigma_force != 0";
+        return LB_EINVAL;
+    }
+    if (!std::isfinite(G)) { why = "G must be finite"; return LB_EINVAL; }
+    switch (eos->kind) {
+        case LB_EOS_CS:
+            if (!(eos->a > 0 && eos->b > 0 && eos->R > 0 && eos->T > 0)) {
+                why = "Carnahan-Starling needs a, b, R, T > 0";
+                return LB_EINVAL;
+            }
+            if (G == 0.0) { why = "G must be non-zero for the EOS-based potential"; return LB_EINVAL; }
+            break;
+        case LB_EOS_EXP:
+            if (!(eos->psi0 > 0 && eos->rho0 > 0)) { why = "exponential potential needs psi0, rho0 > 0"; return LB_EINVAL; }
+            break;
+        case LB_EOS_PIECEWISE:
+            if (!(eos->rho1 > 0 && eos->rho2 > eos->rho1)) { why = "Eq. 23 needs 0 < rho1 < rho2"; return LB_EINVAL; }
+            if (G == 0.0) { why = "G must be non-zero for the EOS-based potential"; return LB_EINVAL; }
+            break;
+        default:
+            why = "unknown EOS kind";
+            return LB_EINVAL;
+    }
+    return LB_OK;
+}
+
+Consts make_consts(const lb_eos *e, double G, double kappa, double sigma, const lb_rates *r) {
+    Consts c{};
+    c.eos_kind = e->kind;
+    c.a = e->a;
+    c.b4 = e->b / 4.0;
+    c.RT = e->R * e->T;
+    c.psi0 = e->psi0;
+    c.rho0 = e->rho0;
+    c.th_v = e->theta_v;
+    c.th_m = e->theta_m;
+    c.th_l = e->theta_l;
+    c.rho1 = e->rho1;
+    c.rho2 = e->rho2;
+    c.p_rho1 = e->rho1 * e->theta_v;
+    c.p_rho2 = c.p_rho1 + (e->rho2 - e->rho1) * e->theta_m;
+    c.two_over_G = (G != 0.0) ? 2.0 / G : 0.0;
+    c.G = G;
+    c.kG2 = kappa * G / 2.0;
+    const double tau_e = 1.0 / r->s_e;
+    c.sig_coef = 12.0 * sigma * G * G / (tau_e - 0.5);
+    c.s_e = r->s_e;
+    c.s_z = r->s_zeta;
+    c.s_q = r->s_q;
+    c.s_v = r->s_v;
+    return c;
+}
+
+lb_status check_usable(lb_ctx *c) {
+    if (!c) return LB_EINVAL;
+    return c->sticky;
+}
+
+// Wait for the stream and fold device error bits into the sticky status.
+lb_status sync_and_check(lb_ctx *c) {
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    int flags = 0;
+    LB_CUDA(c, cudaMemcpy(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags & lbm::ERR_DOMAIN)
+        return poison(c, LB_EDOMAIN, "psi^2 < 0 or rho <= 0 at some site (EOS domain left)");
+    return LB_OK;
+}
+
+lb_status ensure_diag(lb_ctx *c) {
+    const size_t n = (size_t)c->geom.nx * c->geom.ny;
+    if (!c->d_psi) LB_CUDA(c, cudaMalloc(&c->d_psi, n * sizeof(double)));
+    if (!c->d_field) LB_CUDA(c, cudaMalloc(&c->d_field, n * sizeof(double)));
+    if (!c->d_partials)
+        LB_CUDA(c, cudaMalloc(&c->d_partials, 4 * sizeof(double) * lbm::reduce_blocks((long long)n)));
+    if (!c->d_out4) LB_CUDA(c, cudaMalloc(&c->d_out4, 4 * sizeof(double)));
+    return LB_OK;
+}
+
+lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
+                 double sigma, const lb_rates *rates, int prec, int bc, void *stream, void *fa,
+                 void *fb, bool external) {
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    std::string why;
+    lb_status s = validate(nx, ny, eos, G, kappa, sigma, rates, prec, bc, why);
+    if (s != LB_OK) {
+        std::fprintf(stderr, "lb_init: %s\n", why.c_str());
+        return s;
+    }
+    if (external) {
+        if (!fa || !fb || fa == fb) return LB_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(fa) | reinterpret_cast<uintptr_t>(fb)) & 255u) return LB_EINVAL;
+    }
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_ENOMEM;
+    c->prec = prec;
+    c->elem = elem_size(prec);
+    c->geom.nx = nx;
+    c->geom.ny = ny;
+    c->geom.pitch = (int)lb_pitch(nx, prec);
+    c->geom.plane = (long long)ny * c->geom.pitch;
+    c->geom.walls = (bc == LB_BC_WALLS_Y) ? 1 : 0;
+    c->consts = make_consts(eos, G, kappa, sigma, rates);
+    c->stream = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "lb_init: %s\n", cudaGetErrorString(e));
+        delete c;
+        return LB_ECUDA;
+    }
+    c->launch = lbm::default_step_launch(c->geom, sms);
+    const size_t bytes = lb_buffer_bytes(nx, ny, prec);
+    if (external) {
+        c->f[0] = fa;
+        c->f[1] = fb;
+        c->own_f = false;
+    } else {
+        c->own_f = true;
+        if (cudaMalloc(&c->f[0], bytes) != cudaSuccess || cudaMalloc(&c->f[1], bytes) != cudaSuccess) {
+            lb_free(c);
+            return LB_ENOMEM;
+        }
+    }
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
+        lb_free(c);
+        return LB_ENOMEM;
+    }
+    if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->f[0], 0, bytes, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->f[1], 0, bytes, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        lb_free(c);
+        return LB_ECUDA;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_pitch(int nx, int prec) {
+    (void)prec;
+    if (nx <= 0) return 0;
+    return (size_t)((nx + 31) / 32) * 32;
+}
+
+size_t lb_buffer_bytes(int nx, int ny, int prec) {
+    if (nx <= 0 || ny <= 0) return 0;
+    return 9 * (size_t)ny * lb_pitch(nx, prec) * elem_size(prec);
+}
+
+lb_status lb_init(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
+                  double sigma_force, const lb_rates *rates, int prec, int bc, void *stream) {
+    return create(out, nx, ny, eos, G, kappa, sigma_force, rates, prec, bc, stream, nullptr,
+                  nullptr, false);
+}
+
+lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
+                     double sigma_force, const lb_rates *rates, int prec, int bc, void *stream,
+                     void *f_a, void *f_b) {
+    return create(out, nx, ny, eos, G, kappa, sigma_force, rates, prec, bc, stream, f_a, f_b,
+                  true);
+}
+
+lb_status lb_set_rho_u(lb_ctx *c, const double *rho, const double *ux, const double *uy) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!rho || !ux || !uy) return fail(c, LB_EINVAL, "lb_set_rho_u: NULL array");
+    const size_t n = (size_t)c->geom.nx * c->geom.ny;
+    if (!c->d_host_in) LB_CUDA(c, cudaMalloc(&c->d_host_in, 3 * n * sizeof(double)));
+    LB_CUDA(c, cudaMemcpyAsync(c->d_host_in, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(c->d_host_in + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(c->d_host_in + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, lbm::launch_init_feq(c->prec, c->consts, c->geom, c->d_host_in, c->d_host_in + n,
+                                    c->d_host_in + 2 * n, c->f[c->cur], c->d_err, c->stream));
+    c->steps = 0;
+    return sync_and_check(c);
+}
+
+lb_status lb_step(lb_ctx *c, int n) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (n < 0) return fail(c, LB_EINVAL, "lb_step: n < 0");
+    for (int i = 0; i < n; ++i) {
+        LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, c->f[c->cur],
+                                    c->f[c->cur ^ 1], c->d_err, c->stream));
+        c->cur ^= 1;
+        ++c->steps;
+    }
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx *c) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    return sync_and_check(c);
+}
+
+lb_status lb_get_rho(lb_ctx *c, double *rho) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!rho) return fail(c, LB_EINVAL, "lb_get_rho: NULL");
+    if ((s = ensure_diag(c)) != LB_OK) return s;
+    const size_t n = (size_t)c->geom.nx * c->geom.ny;
+    // density only: the macro kernel skips psi when no velocity output is requested
+    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                        c->d_field, nullptr, nullptr, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(rho, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+lb_status lb_get_u(lb_ctx *c, double *ux, double *uy) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!ux || !uy) return fail(c, LB_EINVAL, "lb_get_u: NULL");
+    if ((s = ensure_diag(c)) != LB_OK) return s;
+    const size_t n = (size_t)c->geom.nx * c->geom.ny;
+    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                     c->d_err, c->stream));
+    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                        nullptr, c->d_field, nullptr, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(ux, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                        nullptr, nullptr, c->d_field, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(uy, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+lb_status lb_get_populations(lb_ctx *c, void *dst, size_t bytes) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    const size_t row = (size_t)c->geom.nx * c->elem;
+    if (!dst || bytes != 9 * (size_t)c->geom.ny * row)
+        return fail(c, LB_EINVAL, "lb_get_populations: NULL or size mismatch");
+    LB_CUDA(c, cudaMemcpy2DAsync(dst, row, c->f[c->cur], (size_t)c->geom.pitch * c->elem, row,
+                                 9 * (size_t)c->geom.ny, cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+lb_status lb_set_populations(lb_ctx *c, const void *src, size_t bytes) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    const size_t row = (size_t)c->geom.nx * c->elem;
+    if (!src || bytes != 9 * (size_t)c->geom.ny * row)
+        return fail(c, LB_EINVAL, "lb_set_populations: NULL or size mismatch");
+    LB_CUDA(c, cudaMemcpy2DAsync(c->f[c->cur], (size_t)c->geom.pitch * c->elem, src, row, row,
+                                 9 * (size_t)c->geom.ny, cudaMemcpyHostToDevice, c->stream));
+    return sync_and_check(c);
+}
+
+lb_status lb_reduce(lb_ctx *c, double out[4]) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!out) return fail(c, LB_EINVAL, "lb_reduce: NULL");
+    if ((s = ensure_diag(c)) != LB_OK) return s;
+    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                     c->d_err, c->stream));
+    LB_CUDA(c, lbm::launch_macro_reduce(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+                                        c->d_partials, c->d_out4, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(out, c->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = sync_and_check(c)) != LB_OK) return s;
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(out[i]))
+            return poison(c, LB_ENONFINITE, "lb_reduce: non-finite mass, momentum or |v|");
+    return LB_OK;
+}
+
+long long lb_steps_done(const lb_ctx *c) { return c ? c->steps : 0; }
+
+int lb_kernels_per_step(const lb_ctx *c) { return c ? 1 : 0; }
+
+const char *lb_last_error(const lb_ctx *c) { return c ? c->msg.c_str() : kNoCtx; }
+
+lb_status lb_status_of(const lb_ctx *c) { return c ? c->sticky : LB_EINVAL; }
+
+void lb_free(lb_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->own_f) {
+        cudaFree(c->f[0]);
+        cudaFree(c->f[1]);
+    }
+    cudaFree(c->d_err);
+    cudaFree(c->d_psi);
+    cudaFree(c->d_field);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_out4);
+    cudaFree(c->d_host_in);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Private declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lb.h"
+
+namespace lbm {
+
+// Error bits written by kernels into the context's device flag word.
+enum : int { ERR_DOMAIN = 1 };
+
+// Per-lattice constants of the update, in double; kernels convert them to their type.
+struct Consts {
+    int eos_kind;
+    // Carnahan-Starling: p = rho RT (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2, eta = b4 rho
+    double a, b4, RT;
+    // exponential potential psi0 exp(-rho0/rho)
+    double psi0, rho0;
+    // Eq. 23 branches; p_rho1 = rho1 th_v, p_rho2 = p_rho1 + (rho2 - rho1) th_m
+    double th_v, th_m, th_l, rho1, rho2, p_rho1, p_rho2;
+    // psi^2 = (p - rho/3) * two_over_G for the EOS-based potentials
+    double two_over_G;
+    double G;       // interaction strength of Eq. 7
+    double kG2;     // kappa G / 2 of Eq. 19
+    double sig_coef;  // 12 sigma G^2 / (tau_e - 1/2): Eq. 8 with |F|^2/psi^2 = G^2 |sum w psi e|^2
+    double s_e, s_z, s_q, s_v;  // non-conserved relaxation rates (s_rho, s_j drop out, see kernels)
+};
+
+// Geometry of one lattice's device population buffer.
+struct Geom {
+    int nx, ny;
+    int pitch;          // elements per row
+    long long plane;    // elements per population plane = ny * pitch
+    int walls;          // 0 periodic in y, 1 bounce-back walls in y
+};
+
+struct StepLaunch {
+    int tx;             // columns per CTA (threads)
+    int rows;           // rows each CTA marches over
+};
+
+// ---- kernels (lb_kernels.cu) -------------------------------------------------------
+// All launches go to `stream`; they return cudaGetLastError() of the launch.
+cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l,
+                        const void *fin, void *fout, int *err, cudaStream_t stream);
+cudaError_t launch_init_feq(int prec, const Consts &c, const Geom &g, const double *rho,
+                            const double *ux, const double *uy, void *f, int *err,
+                            cudaStream_t stream);
+cudaError_t launch_psi_field(int prec, const Consts &c, const Geom &g, const void *f,
+                             double *psi, int *err, cudaStream_t stream);
+cudaError_t launch_macro_fields(int prec, const Consts &c, const Geom &g, const void *f,
+                                const double *psi, double *rho, double *ux, double *uy,
+                                cudaStream_t stream);
+// Deterministic FP64 reduction: partials must hold 4 * reduce_blocks(n) doubles.
+int reduce_blocks(long long n_sites);
+cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const void *f,
+                                const double *psi, double *partials, double *out4,
+                                cudaStream_t stream);
+
+StepLaunch default_step_launch(const Geom &g, int num_sms);
+
+// ---- host thermodynamics (lb_thermo.cpp) ---------------------------------------------
+double p_eos_host(const lb_eos &e, double G, double rho);
+
+}  // namespace lbm

@@ -1,0 +1,358 @@
+"""Python binding of the C ABI in include/lb.h (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/liblb_gb300.so``. When the library
+is missing this module raises at first use; there is no CPU fallback.
+
+Low-level functions keep the C names (``lb_init``, ``lb_step``, ``lb_get_rho`` ...).
+``Lattice`` wraps one context; by default its two population buffers are device
+memory allocated through PyTorch and its work goes to PyTorch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblb_gb300.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EDOMAIN, LB_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
+                5: "LB_EDOMAIN", 6: "LB_ETIMEOUT"}
+LB_EOS_CS, LB_EOS_EXP, LB_EOS_PIECEWISE = 0, 1, 2
+LB_FP64, LB_FP32 = 0, 1
+LB_BC_PERIODIC, LB_BC_WALLS_Y = 0, 1
+
+# every exported symbol of include/lb.h
+EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_u", "lb_step",
+            "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
+            "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
+            "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell"]
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {message}".rstrip())
+
+
+class c_lb_eos(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
+                ("T", C.c_double), ("psi0", C.c_double), ("rho0", C.c_double),
+                ("theta_v", C.c_double), ("theta_m", C.c_double), ("theta_l", C.c_double),
+                ("rho1", C.c_double), ("rho2", C.c_double)]
+
+
+class c_lb_rates(C.Structure):
+    _fields_ = [("s_rho", C.c_double), ("s_e", C.c_double), ("s_zeta", C.c_double),
+                ("s_j", C.c_double), ("s_q", C.c_double), ("s_v", C.c_double)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing ({LIB_PATH}); build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, SZ = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    DP = C.POINTER(C.c_double)
+    sig = {
+        "lb_pitch": (SZ, [I, I]),
+        "lb_buffer_bytes": (SZ, [I, I, I]),
+        "lb_init": (I, [C.POINTER(P), I, I, C.POINTER(c_lb_eos), D, D, D, C.POINTER(c_lb_rates),
+                        I, I, P]),
+        "lb_init_ex": (I, [C.POINTER(P), I, I, C.POINTER(c_lb_eos), D, D, D,
+                           C.POINTER(c_lb_rates), I, I, P, P, P]),
+        "lb_set_rho_u": (I, [P, DP, DP, DP]),
+        "lb_step": (I, [P, I]),
+        "lb_sync": (I, [P]),
+        "lb_get_rho": (I, [P, DP]),
+        "lb_get_u": (I, [P, DP, DP]),
+        "lb_get_populations": (I, [P, P, SZ]),
+        "lb_set_populations": (I, [P, P, SZ]),
+        "lb_reduce": (I, [P, DP]),
+        "lb_steps_done": (C.c_longlong, [P]),
+        "lb_kernels_per_step": (I, [P]),
+        "lb_last_error": (C.c_char_p, [P]),
+        "lb_status_of": (I, [P]),
+        "lb_free": (None, [P]),
+        "lb_cs_critical": (I, [D, D, D, DP, DP]),
+        "lb_maxwell": (I, [C.POINTER(c_lb_eos), D, DP, DP, DP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != LB_OK:
+        msg = ""
+        if ctx is not None:
+            raw = load_library().lb_last_error(ctx)
+            msg = raw.decode() if raw else ""
+        raise LBError(status, where, msg)
+
+
+# ------------------------------------------------------------------------------------
+# parameters
+# ------------------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class EOSParams:
+    """Mirror of lb_eos. kind: "cs" | "exp" | "piecewise"."""
+
+    kind: str = "cs"
+    a: float = 1.0
+    b: float = 4.0
+    R: float = 1.0
+    T: float = 0.0
+    psi0: float = 4.0
+    rho0: float = 200.0
+    theta_v: float = 0.49 / 3.0
+    theta_m: float = -0.06 / 3.0
+    theta_l: float = 1.0 / 3.0
+    rho1: float = 1.49
+    rho2: float = 94.65
+
+    def to_c(self) -> c_lb_eos:
+        kinds = {"cs": LB_EOS_CS, "exp": LB_EOS_EXP, "piecewise": LB_EOS_PIECEWISE}
+        return c_lb_eos(kinds[self.kind], self.a, self.b, self.R, self.T, self.psi0, self.rho0,
+                        self.theta_v, self.theta_m, self.theta_l, self.rho1, self.rho2)
+
+
+@dataclass(frozen=True)
+class RateParams:
+    """Mirror of lb_rates (s = 1/tau)."""
+
+    s_rho: float = 1.0
+    s_e: float = 0.8
+    s_zeta: float = 0.8
+    s_j: float = 1.0
+    s_q: float = 1.1
+    s_v: float = 1.0 / 0.8
+
+    def to_c(self) -> c_lb_rates:
+        return c_lb_rates(self.s_rho, self.s_e, self.s_zeta, self.s_j, self.s_q, self.s_v)
+
+    @staticmethod
+    def from_viscosity(nu: float, **kw) -> "RateParams":
+        return RateParams(s_v=1.0 / (3.0 * nu + 0.5), **kw)
+
+
+def lb_cs_critical(a: float = 1.0, b: float = 4.0, R: float = 1.0):
+    Tc, rc = C.c_double(), C.c_double()
+    _check(load_library().lb_cs_critical(a, b, R, C.byref(Tc), C.byref(rc)), "lb_cs_critical")
+    return Tc.value, rc.value
+
+
+def cs_eos(t_over_tc: float, a: float = 1.0, b: float = 4.0, R: float = 1.0) -> EOSParams:
+    Tc, _ = lb_cs_critical(a, b, R)
+    return EOSParams(kind="cs", a=a, b=b, R=R, T=t_over_tc * Tc)
+
+
+def lb_maxwell(eos: EOSParams, G: float):
+    rv, rl, pb = C.c_double(), C.c_double(), C.c_double()
+    e = eos.to_c()
+    _check(load_library().lb_maxwell(C.byref(e), G, C.byref(rv), C.byref(rl), C.byref(pb)),
+           "lb_maxwell")
+    return rv.value, rl.value, pb.value
+
+
+def lb_pitch(nx: int, prec: int) -> int:
+    return int(load_library().lb_pitch(nx, prec))
+
+
+def lb_buffer_bytes(nx: int, ny: int, prec: int) -> int:
+    return int(load_library().lb_buffer_bytes(nx, ny, prec))
+
+
+# ------------------------------------------------------------------------------------
+# context wrappers with the C names
+# ------------------------------------------------------------------------------------
+
+def lb_init(nx, ny, eos: EOSParams, G, kappa, sigma_force, rates: RateParams, prec, bc,
+            stream=None):
+    lib = load_library()
+    ctx = C.c_void_p()
+    e, r = eos.to_c(), rates.to_c()
+    _check(lib.lb_init(C.byref(ctx), nx, ny, C.byref(e), G, kappa, sigma_force, C.byref(r),
+                       prec, bc, stream), "lb_init")
+    return ctx
+
+
+def lb_init_ex(nx, ny, eos: EOSParams, G, kappa, sigma_force, rates: RateParams, prec, bc,
+               stream, f_a_ptr: int, f_b_ptr: int):
+    lib = load_library()
+    ctx = C.c_void_p()
+    e, r = eos.to_c(), rates.to_c()
+    _check(lib.lb_init_ex(C.byref(ctx), nx, ny, C.byref(e), G, kappa, sigma_force, C.byref(r),
+                          prec, bc, stream, C.c_void_p(f_a_ptr), C.c_void_p(f_b_ptr)),
+           "lb_init_ex")
+    return ctx
+
+
+def lb_set_rho_u(ctx, rho, ux, uy):
+    rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    _check(load_library().lb_set_rho_u(ctx, _dp(rho), _dp(ux), _dp(uy)), "lb_set_rho_u", ctx)
+
+
+def lb_step(ctx, n: int):
+    _check(load_library().lb_step(ctx, int(n)), "lb_step", ctx)
+
+
+def lb_sync(ctx):
+    _check(load_library().lb_sync(ctx), "lb_sync", ctx)
+
+
+def lb_get_rho(ctx, out: np.ndarray):
+    _check(load_library().lb_get_rho(ctx, _dp(out)), "lb_get_rho", ctx)
+    return out
+
+
+def lb_get_u(ctx, ux: np.ndarray, uy: np.ndarray):
+    _check(load_library().lb_get_u(ctx, _dp(ux), _dp(uy)), "lb_get_u", ctx)
+    return ux, uy
+
+
+def lb_get_populations(ctx, dst_ptr: int, nbytes: int):
+    _check(load_library().lb_get_populations(ctx, C.c_void_p(dst_ptr), nbytes),
+           "lb_get_populations", ctx)
+
+
+def lb_set_populations(ctx, src_ptr: int, nbytes: int):
+    _check(load_library().lb_set_populations(ctx, C.c_void_p(src_ptr), nbytes),
+           "lb_set_populations", ctx)
+
+
+def lb_reduce(ctx):
+    out = np.zeros(4)
+    _check(load_library().lb_reduce(ctx, _dp(out)), "lb_reduce", ctx)
+    return out
+
+
+def lb_steps_done(ctx) -> int:
+    return int(load_library().lb_steps_done(ctx))
+
+
+def lb_kernels_per_step(ctx) -> int:
+    return int(load_library().lb_kernels_per_step(ctx))
+
+
+def lb_status_of(ctx) -> int:
+    return int(load_library().lb_status_of(ctx))
+
+
+def lb_last_error(ctx) -> str:
+    raw = load_library().lb_last_error(ctx)
+    return raw.decode() if raw else ""
+
+
+def lb_free(ctx):
+    if ctx:
+        load_library().lb_free(ctx)
+
+
+# ------------------------------------------------------------------------------------
+# convenience wrapper
+# ------------------------------------------------------------------------------------
+
+@dataclass
+class Lattice:
+    """One lattice on the current CUDA device.
+
+    buffers="torch": the two population buffers are torch uint8 device tensors and the
+    work runs on torch's current stream (lb_init_ex). buffers="library": lb_init
+    allocates them and uses the legacy default stream."""
+
+    nx: int
+    ny: int
+    eos: EOSParams
+    G: float
+    kappa: float = 0.0
+    sigma_force: float = 0.0
+    rates: RateParams = field(default_factory=RateParams)
+    prec: str = "fp64"
+    walls_y: bool = False
+    buffers: str = "torch"
+
+    def __post_init__(self):
+        self._prec = LB_FP32 if self.prec == "fp32" else LB_FP64
+        self.dtype = np.float32 if self._prec == LB_FP32 else np.float64
+        bc = LB_BC_WALLS_Y if self.walls_y else LB_BC_PERIODIC
+        self._tensors = None
+        if self.buffers == "torch":
+            import torch
+            nbytes = lb_buffer_bytes(self.nx, self.ny, self._prec)
+            a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            self._tensors = (a, b)
+            self.stream = torch.cuda.current_stream().cuda_stream
+            self.ctx = lb_init_ex(self.nx, self.ny, self.eos, self.G, self.kappa,
+                                  self.sigma_force, self.rates, self._prec, bc, self.stream,
+                                  a.data_ptr(), b.data_ptr())
+        else:
+            self.stream = None
+            self.ctx = lb_init(self.nx, self.ny, self.eos, self.G, self.kappa, self.sigma_force,
+                               self.rates, self._prec, bc, None)
+
+    # --- state
+    def set_rho_u(self, rho, ux=None, uy=None):
+        z = np.zeros((self.ny, self.nx))
+        lb_set_rho_u(self.ctx, rho, z if ux is None else ux, z if uy is None else uy)
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=self.dtype)
+        assert f.shape == (9, self.ny, self.nx)
+        lb_set_populations(self.ctx, f.ctypes.data, f.nbytes)
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((9, self.ny, self.nx), dtype=self.dtype)
+        lb_get_populations(self.ctx, out.ctypes.data, out.nbytes)
+        return out
+
+    # --- time stepping and diagnostics
+    def step(self, n: int = 1):
+        lb_step(self.ctx, n)
+
+    def sync(self):
+        lb_sync(self.ctx)
+
+    def rho(self) -> np.ndarray:
+        return lb_get_rho(self.ctx, np.empty((self.ny, self.nx)))
+
+    def u(self):
+        return lb_get_u(self.ctx, np.empty((self.ny, self.nx)), np.empty((self.ny, self.nx)))
+
+    def reduce(self) -> np.ndarray:
+        return lb_reduce(self.ctx)
+
+    @property
+    def steps_done(self) -> int:
+        return lb_steps_done(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb_free(self.ctx)
+            self.ctx = None
+        self._tensors = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
