@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1, help="step-kernel variant (-1: library default)")
+    ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
     return ap.parse_args()
 
 
@@ -150,10 +152,13 @@ def droplet_setup(lbm, inputs, nx, ny):
 # native arm
 # --------------------------------------------------------------------------------------
 
-def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist):
+def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist, launch=None):
     eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
     lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec)
+    if launch is not None and launch[0] >= 0:
+        lbm.lb_set_launch(lat.ctx, launch[0], launch[1])
     lat.set_rho_u(rho)
+    shape = lbm.lb_get_launch(lat.ctx)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         lat.step(inner)
@@ -179,7 +184,7 @@ def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist)
     step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
     launches = steps * (inner * lbm.lb_kernels_per_step(lat.ctx) + 3)
     lat.close()
-    return total_ms, step_kernel_ms / (steps * inner), launches
+    return total_ms, step_kernel_ms / (steps * inner), launches, shape
 
 
 def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
@@ -271,8 +276,9 @@ def native(args):
     nx, ny, inner, K, W = args.nx, args.ny, args.inner, args.steps, args.warmup
     sites = nx * ny
     with ClockSampler(local) as clocks:
-        total_ms, kern_ms, launches = time_precision(lbm, torch, inputs, "fp32", nx, ny, inner,
-                                                     K, W, dist)
+        total_ms, kern_ms, launches, shape = time_precision(lbm, torch, inputs, "fp32", nx, ny,
+                                                            inner, K, W, dist,
+                                                            (args.variant, args.rows))
     t = torch.tensor([total_ms], device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -285,16 +291,17 @@ def native(args):
     traffic = profiled_traffic("fp32")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic,
-            "kernel": "k_fused_step<float>", "alg_bytes_per_launch": alg,
+            "kernel": "k_pull_collide<float>", "launch": shape, "alg_bytes_per_launch": alg,
             "kernel_ms": round(kern_ms, 5), "peak_source": f"{peak_src} (copy bandwidth)"}
 
     # FP64 leg
     fk = max(args.fp64_steps, 1)
-    f_total, f_kern, _ = time_precision(lbm, torch, inputs, "fp64", nx, ny, inner, fk, 1, dist)
+    f_total, f_kern, _, shape64 = time_precision(lbm, torch, inputs, "fp64", nx, ny, inner, fk, 1,
+                                                 dist)
     alg64 = ALG_BYTES_PER_SITE["fp64"] * sites
     fp64 = {"value": round(sites * inner * fk / (f_total * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "kernel_ms": round(f_kern, 5),
-            "hbm_frac": round(alg64 / (f_kern * 1e-3) / 1e9 / hbm, 4),
+            "hbm_frac": round(alg64 / (f_kern * 1e-3) / 1e9 / hbm, 4), "launch": shape64,
             "note": "FP64 update is bound by FP64 ALU throughput on GB300, not HBM"}
 
     e2e = None

@@ -20,7 +20,12 @@
  *   the caller. Host population arrays are [alpha][y][x], 9 * ny * nx elements of
  *   the context's storage type (double for LB_FP64, float for LB_FP32).
  * - Populations are stored on the device as 9 planes of ny rows of `pitch`
- *   elements (pitch = lb_pitch(nx, prec) >= nx, a multiple of 32 elements).
+ *   elements (pitch = lb_pitch(nx, prec) >= nx + 8, a multiple of 32 elements).
+ *   Column x of a row sits at element x + 4; elements 2, 3 and nx+4, nx+5 hold
+ *   periodic images of columns nx-2, nx-1 and 0, 1. The stored array is the state
+ *   g from which the populations of the current time are PULLED,
+ *   f_a(x, t) = g_a(x - e_a) (bounce-back at walls), i.e. the post-collision values
+ *   of the previous step before streaming. lb_get/set_populations convert.
  * - Every function returns an lb_status; nothing throws across the ABI. After
  *   LB_ENONFINITE, LB_EDOMAIN or LB_ETIMEOUT the context is poisoned: every later
  *   call except lb_free / lb_last_error / lb_status_of returns that code again.
@@ -103,15 +108,34 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
                      double sigma_force, const lb_rates *rates, int prec, int bc, void *stream,
                      void *f_a, void *f_b);
 
+/* Number of compiled variants of the step kernel (strip width x shared-memory ring depth). */
+int lb_launch_variants(void);
+
+/* Choose the step kernel's variant (0 .. lb_launch_variants()-1) and the number of rows
+ * each CTA marches over (rows = 0: size the grid to one full wave of resident CTAs).
+ * Synchronises the stream. Errors: LB_EINVAL for an unknown variant or rows < 0. */
+lb_status lb_set_launch(lb_ctx *ctx, int variant, int rows);
+
+/* Current launch: variant, lattice columns per CTA, rows per CTA, resident CTAs per SM. */
+lb_status lb_get_launch(const lb_ctx *ctx, int *variant, int *tx, int *rows, int *ctas_per_sm);
+
+/* Test hook for the failure path of the bounded device-side waits: from the next lb_step
+ * on, the step kernel never requests lattice row `row` (as staged in its shared-memory
+ * ring), so the CTAs that need it give up after about one second and the next
+ * synchronising call returns LB_ETIMEOUT. Nothing faults and no copy is left in flight.
+ * INT_MIN (the default) switches it off. Not part of the method; for tests only. */
+lb_status lb_debug_stall_row(lb_ctx *ctx, int row);
+
 /* f = f_eq(rho, u) = M^-1 m_eq(rho, u) of Eq. 3 at every site (the initial state).
  * rho, ux, uy: host arrays of nx*ny doubles, [y][x]. The step counter is reset to 0.
  * Synchronises the stream. Errors: LB_EINVAL (NULL), LB_EDOMAIN if psi(rho) is not real
- * at some site (rho <= 0, or (p_EOS - rho/3)/G < 0), LB_ECUDA. */
+ * and positive at some site (rho <= 0, or (p_EOS - rho/3)/G <= 0), LB_ECUDA. */
 lb_status lb_set_rho_u(lb_ctx *ctx, const double *rho, const double *ux, const double *uy);
 
-/* Advance n >= 0 time steps (Eqs. 4-8, 17-19). Queued on the stream; returns without
- * waiting. A psi-domain violation found on the device is reported by the next call
- * that synchronises (lb_sync, lb_get_*, lb_reduce) as LB_EDOMAIN. */
+/* Advance n >= 0 time steps (Eqs. 4-8, 17-19), one kernel launch per step. Queued on the
+ * stream; returns without waiting. A psi-domain violation found on the device is reported
+ * by the next call that synchronises (lb_sync, lb_get_*, lb_reduce) as LB_EDOMAIN; a
+ * device-side wait that gave up (about one second) as LB_ETIMEOUT. */
 lb_status lb_step(lb_ctx *ctx, int n);
 
 /* Wait for queued work and report device-side errors (LB_EDOMAIN, LB_ECUDA). */

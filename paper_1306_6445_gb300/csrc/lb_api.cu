@@ -1,10 +1,13 @@
 // C ABI of the library (declared in include/lb.h): context management, argument
-// validation, device buffers and the host side of every call.
+// validation, device buffers, TMA descriptors and the host side of every call.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 
 #include "lb_internal.h"
@@ -19,11 +22,12 @@ struct lb_ctx {
     size_t elem = 8;
     cudaStream_t stream = nullptr;
     void *f[2] = {nullptr, nullptr};
+    alignas(64) CUtensorMap tmap[2];  // TMA descriptors of f[0] and f[1]
     bool own_f = false;
-    int cur = 0;                 // index of the buffer holding the current populations
+    int cur = 0;                 // buffer holding the current state g (f = pull of g)
+    int num_sms = 0;
     int *d_err = nullptr;        // device error bits
-    double *d_psi = nullptr;     // diagnostics: psi field (nx*ny), allocated on first use
-    double *d_field = nullptr;   // diagnostics: one nx*ny double field
+    double *d_field = nullptr;   // diagnostics: two nx*ny double fields
     double *d_partials = nullptr;
     double *d_out4 = nullptr;
     double *d_host_in = nullptr; // 3*nx*ny staging for lb_set_rho_u
@@ -67,7 +71,7 @@ bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
 lb_status validate(int nx, int ny, const lb_eos *eos, double G, double kappa, double sigma,
                    const lb_rates *r, int prec, int bc, std::string &why) {
     if (nx < 3 || ny < 3) { why = "nx and ny must be >= 3"; return LB_EINVAL; }
-    if ((long long)nx * ny > (1LL << 31) - 1) { why = "lattice too large"; return LB_EINVAL; }
+    if ((long long)(nx + 2 * lbm::kGhost + 32) * ny > (1LL << 31) - 1) { why = "lattice too large"; return LB_EINVAL; }
     if (!eos || !r) { why = "eos and rates must not be NULL"; return LB_EINVAL; }
     if (prec != LB_FP32 && prec != LB_FP64) { why = "prec must be LB_FP64 or LB_FP32"; return LB_EINVAL; }
     if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y) { why = "bad boundary kind"; return LB_EINVAL; }
@@ -129,7 +133,62 @@ Consts make_consts(const lb_eos *e, double G, double kappa, double sigma, const 
     c.s_z = r->s_zeta;
     c.s_q = r->s_q;
     c.s_v = r->s_v;
+    c.stall_row = INT_MIN;
     return c;
+}
+
+// ---- TMA descriptors ------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 3-D map over one population buffer: (padded column, row, population); one box is a
+// full lattice row of the strip plus its apron: (tx + 8) x 1 x 9.
+lb_status make_maps(lb_ctx *c) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(c, LB_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const Geom &g = c->geom;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * c->elem, (cuuint64_t)g.plane * c->elem};
+    const cuuint32_t box[3] = {(cuuint32_t)(c->launch.tx + 8), 1, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        c->prec == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = enc(&c->tmap[b], dt, 3, c->f[b], dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            char buf[96];
+            std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+            return fail(c, LB_ECUDA, buf);
+        }
+    }
+    return LB_OK;
+}
+
+lb_status apply_launch(lb_ctx *c, int variant, int rows) {
+    if (variant < 0 || variant >= lbm::step_variant_count())
+        return fail(c, LB_EINVAL, "unknown launch variant");
+    if (rows < 0) return fail(c, LB_EINVAL, "rows must be >= 0");
+    c->launch = lbm::make_step_launch(c->prec, c->consts.eos_kind, c->geom, c->num_sms, variant, rows);
+    LB_CUDA(c, lbm::configure_step(c->prec, c->consts, c->geom, c->launch));
+    return make_maps(c);
 }
 
 lb_status check_usable(lb_ctx *c) {
@@ -142,6 +201,8 @@ lb_status sync_and_check(lb_ctx *c) {
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     int flags = 0;
     LB_CUDA(c, cudaMemcpy(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags & lbm::ERR_TIMEOUT)
+        return poison(c, LB_ETIMEOUT, "a bounded device-side wait gave up");
     if (flags & lbm::ERR_DOMAIN)
         return poison(c, LB_EDOMAIN, "psi^2 < 0 or rho <= 0 at some site (EOS domain left)");
     return LB_OK;
@@ -149,13 +210,14 @@ lb_status sync_and_check(lb_ctx *c) {
 
 lb_status ensure_diag(lb_ctx *c) {
     const size_t n = (size_t)c->geom.nx * c->geom.ny;
-    if (!c->d_psi) LB_CUDA(c, cudaMalloc(&c->d_psi, n * sizeof(double)));
-    if (!c->d_field) LB_CUDA(c, cudaMalloc(&c->d_field, n * sizeof(double)));
+    if (!c->d_field) LB_CUDA(c, cudaMalloc(&c->d_field, 2 * n * sizeof(double)));
     if (!c->d_partials)
         LB_CUDA(c, cudaMalloc(&c->d_partials, 4 * sizeof(double) * lbm::reduce_blocks((long long)n)));
     if (!c->d_out4) LB_CUDA(c, cudaMalloc(&c->d_out4, 4 * sizeof(double)));
     return LB_OK;
 }
+
+void *spare(lb_ctx *c) { return c->f[c->cur ^ 1]; }
 
 lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, double kappa,
                  double sigma, const lb_rates *rates, int prec, int bc, void *stream, void *fa,
@@ -183,15 +245,14 @@ lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, doub
     c->geom.walls = (bc == LB_BC_WALLS_Y) ? 1 : 0;
     c->consts = make_consts(eos, G, kappa, sigma, rates);
     c->stream = static_cast<cudaStream_t>(stream);
-    int dev = 0, sms = 0;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         std::fprintf(stderr, "lb_init: %s\n", cudaGetErrorString(e));
         delete c;
         return LB_ECUDA;
     }
-    c->launch = lbm::default_step_launch(c->geom, sms);
     const size_t bytes = lb_buffer_bytes(nx, ny, prec);
     if (external) {
         c->f[0] = fa;
@@ -215,6 +276,11 @@ lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, doub
         lb_free(c);
         return LB_ECUDA;
     }
+    if ((s = apply_launch(c, 0, 0)) != LB_OK) {
+        std::fprintf(stderr, "lb_init: %s\n", c->msg.c_str());
+        lb_free(c);
+        return s;
+    }
     *out = c;
     return LB_OK;
 }
@@ -226,7 +292,7 @@ extern "C" {
 size_t lb_pitch(int nx, int prec) {
     (void)prec;
     if (nx <= 0) return 0;
-    return (size_t)((nx + 31) / 32) * 32;
+    return (size_t)((nx + 2 * lbm::kGhost + 31) / 32) * 32;
 }
 
 size_t lb_buffer_bytes(int nx, int ny, int prec) {
@@ -247,6 +313,31 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
                   true);
 }
 
+int lb_launch_variants(void) { return lbm::step_variant_count(); }
+
+lb_status lb_set_launch(lb_ctx *c, int variant, int rows) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return apply_launch(c, variant, rows);
+}
+
+lb_status lb_debug_stall_row(lb_ctx *c, int row) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    c->consts.stall_row = row;
+    return LB_OK;
+}
+
+lb_status lb_get_launch(const lb_ctx *c, int *variant, int *tx, int *rows, int *ctas_per_sm) {
+    if (!c) return LB_EINVAL;
+    if (variant) *variant = c->launch.variant;
+    if (tx) *tx = c->launch.tx;
+    if (rows) *rows = c->launch.rows;
+    if (ctas_per_sm) *ctas_per_sm = c->launch.ctas_per_sm;
+    return LB_OK;
+}
+
 lb_status lb_set_rho_u(lb_ctx *c, const double *rho, const double *ux, const double *uy) {
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
@@ -257,7 +348,8 @@ lb_status lb_set_rho_u(lb_ctx *c, const double *rho, const double *ux, const dou
     LB_CUDA(c, cudaMemcpyAsync(c->d_host_in + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(c->d_host_in + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(c, lbm::launch_init_feq(c->prec, c->consts, c->geom, c->d_host_in, c->d_host_in + n,
-                                    c->d_host_in + 2 * n, c->f[c->cur], c->d_err, c->stream));
+                                    c->d_host_in + 2 * n, spare(c), c->d_err, c->stream));
+    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], c->stream));
     c->steps = 0;
     return sync_and_check(c);
 }
@@ -267,7 +359,7 @@ lb_status lb_step(lb_ctx *c, int n) {
     if (s != LB_OK) return s;
     if (n < 0) return fail(c, LB_EINVAL, "lb_step: n < 0");
     for (int i = 0; i < n; ++i) {
-        LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, c->f[c->cur],
+        LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, &c->tmap[c->cur],
                                     c->f[c->cur ^ 1], c->d_err, c->stream));
         c->cur ^= 1;
         ++c->steps;
@@ -287,8 +379,7 @@ lb_status lb_get_rho(lb_ctx *c, double *rho) {
     if (!rho) return fail(c, LB_EINVAL, "lb_get_rho: NULL");
     if ((s = ensure_diag(c)) != LB_OK) return s;
     const size_t n = (size_t)c->geom.nx * c->geom.ny;
-    // density only: the macro kernel skips psi when no velocity output is requested
-    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], nullptr,
                                         c->d_field, nullptr, nullptr, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(rho, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return sync_and_check(c);
@@ -300,14 +391,13 @@ lb_status lb_get_u(lb_ctx *c, double *ux, double *uy) {
     if (!ux || !uy) return fail(c, LB_EINVAL, "lb_get_u: NULL");
     if ((s = ensure_diag(c)) != LB_OK) return s;
     const size_t n = (size_t)c->geom.nx * c->geom.ny;
-    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+    // psi goes into the spare population buffer (free between steps)
+    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
                                      c->d_err, c->stream));
-    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
-                                        nullptr, c->d_field, nullptr, c->stream));
+    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
+                                        nullptr, c->d_field, c->d_field + n, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(ux, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    LB_CUDA(c, lbm::launch_macro_fields(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
-                                        nullptr, nullptr, c->d_field, c->stream));
-    LB_CUDA(c, cudaMemcpyAsync(uy, c->d_field, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(uy, c->d_field + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return sync_and_check(c);
 }
 
@@ -317,7 +407,9 @@ lb_status lb_get_populations(lb_ctx *c, void *dst, size_t bytes) {
     const size_t row = (size_t)c->geom.nx * c->elem;
     if (!dst || bytes != 9 * (size_t)c->geom.ny * row)
         return fail(c, LB_EINVAL, "lb_get_populations: NULL or size mismatch");
-    LB_CUDA(c, cudaMemcpy2DAsync(dst, row, c->f[c->cur], (size_t)c->geom.pitch * c->elem, row,
+    LB_CUDA(c, lbm::launch_stream(c->prec, c->geom, c->f[c->cur], spare(c), c->stream));
+    const char *src = static_cast<const char *>(spare(c)) + lbm::kGhost * c->elem;
+    LB_CUDA(c, cudaMemcpy2DAsync(dst, row, src, (size_t)c->geom.pitch * c->elem, row,
                                  9 * (size_t)c->geom.ny, cudaMemcpyDeviceToHost, c->stream));
     return sync_and_check(c);
 }
@@ -328,8 +420,10 @@ lb_status lb_set_populations(lb_ctx *c, const void *src, size_t bytes) {
     const size_t row = (size_t)c->geom.nx * c->elem;
     if (!src || bytes != 9 * (size_t)c->geom.ny * row)
         return fail(c, LB_EINVAL, "lb_set_populations: NULL or size mismatch");
-    LB_CUDA(c, cudaMemcpy2DAsync(c->f[c->cur], (size_t)c->geom.pitch * c->elem, src, row, row,
+    char *dst = static_cast<char *>(spare(c)) + lbm::kGhost * c->elem;
+    LB_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->geom.pitch * c->elem, src, row, row,
                                  9 * (size_t)c->geom.ny, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], c->stream));
     return sync_and_check(c);
 }
 
@@ -338,9 +432,9 @@ lb_status lb_reduce(lb_ctx *c, double out[4]) {
     if (s != LB_OK) return s;
     if (!out) return fail(c, LB_EINVAL, "lb_reduce: NULL");
     if ((s = ensure_diag(c)) != LB_OK) return s;
-    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+    LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
                                      c->d_err, c->stream));
-    LB_CUDA(c, lbm::launch_macro_reduce(c->prec, c->consts, c->geom, c->f[c->cur], c->d_psi,
+    LB_CUDA(c, lbm::launch_macro_reduce(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
                                         c->d_partials, c->d_out4, c->stream));
     LB_CUDA(c, cudaMemcpyAsync(out, c->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if ((s = sync_and_check(c)) != LB_OK) return s;
@@ -367,7 +461,6 @@ void lb_free(lb_ctx *c) {
         cudaFree(c->f[1]);
     }
     cudaFree(c->d_err);
-    cudaFree(c->d_psi);
     cudaFree(c->d_field);
     cudaFree(c->d_partials);
     cudaFree(c->d_out4);

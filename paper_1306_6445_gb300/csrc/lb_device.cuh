@@ -3,6 +3,11 @@
 // Velocity order e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1);
 // moment order (rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy) of the standard D2Q9
 // transformation matrix M (Sec. II). All constants below are written out by hand.
+//
+// The collision works on PAIRS of sites held in a two-lane vector: in FP32 the lanes are
+// packed into one register pair and every add / multiply / fma is a single packed
+// instruction of sm_100-class GPUs (__fadd2_rn, __fmul2_rn, __ffma2_rn, each lane rounded
+// exactly like the scalar operation); in FP64 the two lanes are plain scalar doubles.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,6 +24,7 @@ struct DevConsts {
     T two_over_G;
     T G, kG2, sig_coef;
     T s_e, s_z, s_q, s_v;
+    int stall_row;
 };
 
 template <typename T>
@@ -31,134 +37,209 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.two_over_G = T(c.two_over_G);
     d.G = T(c.G); d.kG2 = T(c.kG2); d.sig_coef = T(c.sig_coef);
     d.s_e = T(c.s_e); d.s_z = T(c.s_z); d.s_q = T(c.s_q); d.s_v = T(c.s_v);
+    d.stall_row = c.stall_row;
     return d;
 }
 
-__device__ __forceinline__ float lb_exp(float v) { return expf(v); }
+// ---- scalar helpers: FP32 uses the hardware approximations (a few ulp, far inside the
+// FP32 error budget), FP64 the IEEE-rounded operations. Every add / multiply / fma is an
+// explicit round-to-nearest intrinsic, so the compiler cannot contract them differently
+// at different inline sites: a site's psi is bitwise the same wherever it is computed. --
+__device__ __forceinline__ float lb_exp(float v) { return __expf(v); }
 __device__ __forceinline__ double lb_exp(double v) { return exp(v); }
-__device__ __forceinline__ float lb_sqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double lb_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float lb_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double lb_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float lb_sqrt_pos(float v) { return __fmul_rn(v, rsqrtf(v)); }   // v > 0
+__device__ __forceinline__ double lb_sqrt_pos(double v) { return __dsqrt_rn(v); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Interaction potential psi(rho) (Sec. II): psi0 exp(-rho0/rho), or
 // sqrt(2 (p_EOS - rho c_s^2) / G) with p_EOS the Carnahan-Starling EOS or Eq. 23.
-// Sets `bad` when rho <= 0 or psi^2 < 0 (the value is then NaN/inf and must not be used).
+// Sets `bad` when rho <= 0 or psi^2 <= 0 (the value is then not usable).
 template <typename T, int EOS>
 __device__ __forceinline__ T eos_psi(T rho, const DevConsts<T> &P, bool &bad) {
     if constexpr (EOS == LB_EOS_EXP) {
         bad |= !(rho > T(0));
-        return P.psi0 * lb_exp(-P.rho0 / rho);
+        return rmul(P.psi0, lb_exp(-lb_div(P.rho0, rho)));
     } else {
         T p;
         if constexpr (EOS == LB_EOS_CS) {
-            const T eta = P.b4 * rho;
-            const T om = T(1) - eta;
-            p = rho * P.RT * (T(1) + eta * (T(1) + eta * (T(1) - eta))) / (om * om * om)
-                - P.a * rho * rho;
+            // rho RT (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2
+            const T eta = rmul(P.b4, rho);
+            const T om = rsub(T(1), eta);
+            const T poly = rfma(eta, rfma(eta, rsub(T(1), eta), T(1)), T(1));
+            const T num = rmul(rmul(rho, P.RT), poly);
+            p = rsub(lb_div(num, rmul(rmul(om, om), om)), rmul(P.a, rmul(rho, rho)));
         } else {
-            p = (rho <= P.rho1) ? rho * P.th_v
-              : (rho < P.rho2) ? P.p_rho1 + (rho - P.rho1) * P.th_m
-                               : P.p_rho2 + (rho - P.rho2) * P.th_l;
+            p = (rho <= P.rho1) ? rmul(rho, P.th_v)
+              : (rho < P.rho2) ? rfma(rsub(rho, P.rho1), P.th_m, P.p_rho1)
+                               : rfma(rsub(rho, P.rho2), P.th_l, P.p_rho2);
         }
-        const T arg = (p - rho * T(1.0 / 3.0)) * P.two_over_G;
-        bad |= !(arg >= T(0)) || !(rho > T(0));
-        return lb_sqrt(arg);
+        const T arg = rmul(rsub(p, rmul(rho, T(1.0 / 3.0))), P.two_over_G);
+        bad |= !(arg > T(0)) || !(rho > T(0));
+        return lb_sqrt_pos(arg);
     }
 }
 
-// One site's collision: f[9] (post-streaming populations at x) and the potential at x
-// and its eight neighbours pn[a] = psi(x + e_a) (pn[0] = psi(x)) give f*[9] in place.
+// ---- two-lane vectors ---------------------------------------------------------------
+template <typename T>
+struct V2;
+
+template <>
+struct V2<float> {
+    float2 v;
+    __device__ __forceinline__ V2() {}
+    __device__ __forceinline__ V2(float2 a) : v(a) {}
+    __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ static V2 all(float a) { return V2(a, a); }
+    __device__ __forceinline__ float lo() const { return v.x; }
+    __device__ __forceinline__ float hi() const { return v.y; }
+};
+__device__ __forceinline__ V2<float> operator+(V2<float> a, V2<float> b) { return __fadd2_rn(a.v, b.v); }
+__device__ __forceinline__ V2<float> operator*(V2<float> a, V2<float> b) { return __fmul2_rn(a.v, b.v); }
+__device__ __forceinline__ V2<float> operator-(V2<float> a, V2<float> b) {
+    return __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v);   // exactly a - b
+}
+__device__ __forceinline__ V2<float> vfma(V2<float> a, V2<float> b, V2<float> c) {
+    return __ffma2_rn(a.v, b.v, c.v);
+}
+
+template <>
+struct V2<double> {
+    double x, y;
+    __device__ __forceinline__ V2() {}
+    __device__ __forceinline__ V2(double a, double b) : x(a), y(b) {}
+    __device__ __forceinline__ static V2 all(double a) { return V2(a, a); }
+    __device__ __forceinline__ double lo() const { return x; }
+    __device__ __forceinline__ double hi() const { return y; }
+};
+__device__ __forceinline__ V2<double> operator+(V2<double> a, V2<double> b) {
+    return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)};
+}
+__device__ __forceinline__ V2<double> operator*(V2<double> a, V2<double> b) {
+    return {__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)};
+}
+__device__ __forceinline__ V2<double> operator-(V2<double> a, V2<double> b) {
+    return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)};
+}
+__device__ __forceinline__ V2<double> vfma(V2<double> a, V2<double> b, V2<double> c) {
+    return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
+}
+
+// One collision for two sites: f[9] (populations after streaming, pre-collision) and the
+// potential at the sites and their neighbours pn[a] = psi(x + e_a) (pn[0] = psi(x)) give
+// f*[9] in place.
 //
 // Arithmetic (identical in exact arithmetic to Eqs. 3, 5-8, 17-19 and f* = M^-1 m*):
 //   Sx, Sy = sum_a w_a psi(x+e_a) e_a,       F = -G psi(x) (Sx, Sy)                 (Eq. 7)
 //   Q = kappa G/2 psi(x) sum_a w_a (psi_a - psi) e_a e_a                           (Eq. 19)
 //   v = (j + F/2) / rho                                                             (Eq. 6)
 //   |F|^2 / psi^2 in Eq. 8 is evaluated as G^2 (Sx^2 + Sy^2) (no division by psi)
-//   m*_rho = rho and m*_j = j + F for every s_j (the relaxation of j towards
-//   rho v = j + F/2 plus (1 - s_j/2) F cancels s_j exactly), so s_rho and s_j drop out.
+//   m*_rho = rho and m*_j = j + F for every s_j (relaxing j towards rho v = j + F/2 and
+//   adding (1 - s_j/2) F cancels s_j exactly), so s_rho and s_j drop out;
+//   m*_k = (1 - s_k) m_k + s_k m_eq_k + (1 - s_k/2) S_k + C_k for the other moments.
 template <typename T>
-__device__ __forceinline__ void collide_site(T (&f)[9], const T (&pn)[9], const DevConsts<T> &P) {
-    const T pc = pn[0];
-    const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0);
+__device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9],
+                                             const DevConsts<T> &P) {
+    using V = V2<T>;
+    const V third = V::all(T(1.0 / 3.0)), twelfth = V::all(T(1.0 / 12.0));
+    const V two = V::all(T(2)), four = V::all(T(4)), half = V::all(T(0.5));
+    const V pc = pn[0];
 
     // Eq. 7 neighbour sums and Eq. 19 differences
-    const T dg_pp = pn[5] - pn[7];   // (1,1) - (-1,-1)
-    const T dg_mp = pn[6] - pn[8];   // (-1,1) - (1,-1)
-    const T Sx = third * (pn[1] - pn[3]) + twelfth * (dg_pp - dg_mp);
-    const T Sy = third * (pn[2] - pn[4]) + twelfth * (dg_pp + dg_mp);
-    const T Fx = -P.G * pc * Sx;
-    const T Fy = -P.G * pc * Sy;
-    const T dsum = (pn[5] + pn[6]) + (pn[7] + pn[8]) - T(4) * pc;
-    const T qpre = P.kG2 * pc;
-    const T Qxx = qpre * (third * (pn[1] + pn[3] - T(2) * pc) + twelfth * dsum);
-    const T Qyy = qpre * (third * (pn[2] + pn[4] - T(2) * pc) + twelfth * dsum);
-    const T Qxy = qpre * twelfth * ((pn[5] + pn[7]) - (pn[6] + pn[8]));
+    const V dg_pp = pn[5] - pn[7];
+    const V dg_mp = pn[6] - pn[8];
+    const V Sx = vfma(third, pn[1] - pn[3], twelfth * (dg_pp - dg_mp));
+    const V Sy = vfma(third, pn[2] - pn[4], twelfth * (dg_pp + dg_mp));
+    const V mGpc = V::all(-P.G) * pc;
+    const V Fx = mGpc * Sx;
+    const V Fy = mGpc * Sy;
+    const V dsum = ((pn[5] + pn[6]) + (pn[7] + pn[8])) - four * pc;
+    const V qpre = V::all(P.kG2) * pc;
+    const V tdsum = twelfth * dsum;
+    const V Qxx = qpre * vfma(third, (pn[1] + pn[3]) - two * pc, tdsum);
+    const V Qyy = qpre * vfma(third, (pn[2] + pn[4]) - two * pc, tdsum);
+    const V Qxy = qpre * (twelfth * ((pn[5] + pn[7]) - (pn[6] + pn[8])));
 
     // moments m = M f
-    const T ax = f[1] + f[3], ay = f[2] + f[4];
-    const T d13 = f[1] - f[3], d24 = f[2] - f[4];
-    const T s57 = f[5] + f[7], s68 = f[6] + f[8];
-    const T d57 = f[5] - f[7], d68 = f[6] - f[8];
-    const T axis = ax + ay, diag = s57 + s68;
-    const T rho = f[0] + axis + diag;
-    const T jx = d13 + d57 - d68;
-    const T jy = d24 + d57 + d68;
-    const T m1 = T(-4) * f[0] - axis + T(2) * diag;
-    const T m2 = T(4) * f[0] - T(2) * axis + diag;
-    const T m4 = T(-2) * d13 + d57 - d68;
-    const T m6 = T(-2) * d24 + d57 + d68;
-    const T m7 = ax - ay;
-    const T m8 = s57 - s68;
+    const V ax = f[1] + f[3], ay = f[2] + f[4];
+    const V d13 = f[1] - f[3], d24 = f[2] - f[4];
+    const V s57 = f[5] + f[7], s68 = f[6] + f[8];
+    const V d57 = f[5] - f[7], d68 = f[6] - f[8];
+    const V axis = ax + ay, diag = s57 + s68;
+    const V rho = f[0] + (axis + diag);
+    const V jx = d13 + (d57 - d68);
+    const V jy = d24 + (d57 + d68);
+    const V m1 = vfma(two, diag, vfma(V::all(T(-4)), f[0], V::all(T(0)) - axis));
+    const V m2 = vfma(four, f[0], diag - two * axis);
+    const V m4 = vfma(V::all(T(-2)), d13, d57 - d68);
+    const V m6 = vfma(V::all(T(-2)), d24, d57 + d68);
+    const V m7 = ax - ay;
+    const V m8 = s57 - s68;
 
     // Eq. 6 velocity and Eq. 3 equilibria
-    const T rinv = T(1) / rho;
-    const T vx = (jx + T(0.5) * Fx) * rinv;
-    const T vy = (jy + T(0.5) * Fy) * rinv;
-    const T v2 = vx * vx + vy * vy;
-    const T meq1 = rho * (T(-2) + T(3) * v2);
-    const T meq2 = rho * (T(1) - T(3) * v2);
-    const T meq4 = -rho * vx;
-    const T meq6 = -rho * vy;
-    const T meq7 = rho * (vx * vx - vy * vy);
-    const T meq8 = rho * vx * vy;
+    const V rinv(lb_div(T(1), rho.lo()), lb_div(T(1), rho.hi()));
+    const V vx = vfma(half, Fx, jx) * rinv;
+    const V vy = vfma(half, Fy, jy) * rinv;
+    const V vxx = vx * vx, vyy = vy * vy;
+    const V v2 = vxx + vyy;
+    const V meq1 = rho * vfma(V::all(T(3)), v2, V::all(T(-2)));
+    const V meq2 = rho * vfma(V::all(T(-3)), v2, V::all(T(1)));
+    const V rvx = rho * vx, rvy = rho * vy;
+    const V meq7 = rho * (vxx - vyy);
+    const V meq8 = rvx * vy;
 
     // Eq. 5 forcing with S_1 of Eq. 8
-    const T S1 = T(6) * (vx * Fx + vy * Fy) + P.sig_coef * (Sx * Sx + Sy * Sy);
-    const T S7 = T(2) * (vx * Fx - vy * Fy);
-    const T S8 = vx * Fy + vy * Fx;
+    const V S1 = vfma(V::all(T(6)), vfma(vx, Fx, vy * Fy), V::all(P.sig_coef) * vfma(Sx, Sx, Sy * Sy));
+    const V S7 = two * (vx * Fx - vy * Fy);
+    const V S8 = vfma(vx, Fy, vy * Fx);
 
     // Eq. 18 source
-    const T tr = Qxx + Qyy;
+    const V tr = Qxx + Qyy;
 
-    // Eq. 17
-    const T ms0 = rho;
-    const T ms1 = m1 - P.s_e * (m1 - meq1) + (T(1) - T(0.5) * P.s_e) * S1 + T(1.5) * P.s_e * tr;
-    const T ms2 = m2 - P.s_z * (m2 - meq2) - (T(1) - T(0.5) * P.s_z) * S1 - T(1.5) * P.s_z * tr;
-    const T ms3 = jx + Fx;
-    const T ms4 = m4 - P.s_q * (m4 - meq4) - (T(1) - T(0.5) * P.s_q) * Fx;
-    const T ms5 = jy + Fy;
-    const T ms6 = m6 - P.s_q * (m6 - meq6) - (T(1) - T(0.5) * P.s_q) * Fy;
-    const T ms7 = m7 - P.s_v * (m7 - meq7) + (T(1) - T(0.5) * P.s_v) * S7 - P.s_v * (Qxx - Qyy);
-    const T ms8 = m8 - P.s_v * (m8 - meq8) + (T(1) - T(0.5) * P.s_v) * S8 - P.s_v * Qxy;
+    // Eq. 17, written as (1 - s) m + s m_eq + (1 - s/2) S + C
+    const T se = P.s_e, sz = P.s_z, sq = P.s_q, sv = P.s_v;
+    const V ms0 = rho;
+    const V ms1 = vfma(V::all(T(1) - se), m1, vfma(V::all(se), meq1,
+                  vfma(V::all(T(1) - T(0.5) * se), S1, V::all(T(1.5) * se) * tr)));
+    const V ms2 = vfma(V::all(T(1) - sz), m2, vfma(V::all(sz), meq2,
+                  V::all(T(0)) - vfma(V::all(T(1) - T(0.5) * sz), S1, V::all(T(1.5) * sz) * tr)));
+    const V ms3 = jx + Fx;
+    const V ms4 = vfma(V::all(T(1) - sq), m4, V::all(T(0)) - vfma(V::all(sq), rvx, V::all(T(1) - T(0.5) * sq) * Fx));
+    const V ms5 = jy + Fy;
+    const V ms6 = vfma(V::all(T(1) - sq), m6, V::all(T(0)) - vfma(V::all(sq), rvy, V::all(T(1) - T(0.5) * sq) * Fy));
+    const V ms7 = vfma(V::all(T(1) - sv), m7, vfma(V::all(sv), meq7,
+                  vfma(V::all(T(1) - T(0.5) * sv), S7, V::all(-sv) * (Qxx - Qyy))));
+    const V ms8 = vfma(V::all(T(1) - sv), m8, vfma(V::all(sv), meq8,
+                  vfma(V::all(T(1) - T(0.5) * sv), S8, V::all(-sv) * Qxy)));
 
     // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const T c9 = T(1.0 / 9.0), c18 = T(1.0 / 18.0), c36 = T(1.0 / 36.0);
-    const T c6 = T(1.0 / 6.0), c12 = T(1.0 / 12.0), c4 = T(0.25);
-    const T a0 = c9 * ms0;
-    const T base_axis = a0 - c36 * ms1 - c18 * ms2;
-    const T base_diag = a0 + c18 * ms1 + c36 * ms2;
-    const T jx6 = c6 * ms3, qx6 = c6 * ms4, jy6 = c6 * ms5, qy6 = c6 * ms6;
-    const T qx12 = c12 * ms4, qy12 = c12 * ms6;
-    const T pxx4 = c4 * ms7, pxy4 = c4 * ms8;
-    f[0] = a0 - c9 * ms1 + c9 * ms2;
-    f[1] = base_axis + jx6 - qx6 + pxx4;
-    f[3] = base_axis - jx6 + qx6 + pxx4;
-    f[2] = base_axis + jy6 - qy6 - pxx4;
-    f[4] = base_axis - jy6 + qy6 - pxx4;
-    const T xp = jx6 + qx12, yp = jy6 + qy12;
-    f[5] = base_diag + xp + yp + pxy4;
-    f[6] = base_diag - xp + yp - pxy4;
-    f[7] = base_diag - xp - yp + pxy4;
-    f[8] = base_diag + xp - yp - pxy4;
+    const V c9 = V::all(T(1.0 / 9.0)), c18 = V::all(T(1.0 / 18.0)), c36 = V::all(T(1.0 / 36.0));
+    const V c6 = V::all(T(1.0 / 6.0)), c12 = V::all(T(1.0 / 12.0)), c4 = V::all(T(0.25));
+    const V a0 = c9 * ms0;
+    const V base_axis = a0 - vfma(c36, ms1, c18 * ms2);
+    const V base_diag = vfma(c18, ms1, vfma(c36, ms2, a0));
+    const V jx6 = c6 * ms3, qx6 = c6 * ms4, jy6 = c6 * ms5, qy6 = c6 * ms6;
+    const V pxx4 = c4 * ms7, pxy4 = c4 * ms8;
+    const V ax1 = jx6 - qx6, ay1 = jy6 - qy6;
+    f[0] = vfma(c9, ms2 - ms1, a0);
+    f[1] = base_axis + (ax1 + pxx4);
+    f[3] = base_axis + (pxx4 - ax1);
+    f[2] = base_axis + (ay1 - pxx4);
+    f[4] = base_axis - (ay1 + pxx4);
+    const V xp = vfma(c12, ms4, jx6), yp = vfma(c12, ms6, jy6);
+    const V xy_p = xp + yp, xy_m = xp - yp;
+    f[5] = base_diag + (xy_p + pxy4);
+    f[6] = base_diag - (xy_m + pxy4);
+    f[7] = base_diag - (xy_p - pxy4);
+    f[8] = base_diag + (xy_m - pxy4);
 }
 
 }  // namespace lbm

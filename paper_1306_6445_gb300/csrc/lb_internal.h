@@ -10,7 +10,10 @@
 namespace lbm {
 
 // Error bits written by kernels into the context's device flag word.
-enum : int { ERR_DOMAIN = 1 };
+enum : int { ERR_DOMAIN = 1, ERR_TIMEOUT = 2 };
+
+// Ghost columns in front of column 0 of every stored row (periodic images live there).
+constexpr int kGhost = 4;
 
 // Per-lattice constants of the update, in double; kernels convert them to their type.
 struct Consts {
@@ -27,40 +30,51 @@ struct Consts {
     double kG2;     // kappa G / 2 of Eq. 19
     double sig_coef;  // 12 sigma G^2 / (tau_e - 1/2): Eq. 8 with |F|^2/psi^2 = G^2 |sum w psi e|^2
     double s_e, s_z, s_q, s_v;  // non-conserved relaxation rates (s_rho, s_j drop out, see kernels)
+    int stall_row;  // test hook: the step kernel never requests this ring row (INT_MIN = off)
 };
 
 // Geometry of one lattice's device population buffer.
 struct Geom {
     int nx, ny;
-    int pitch;          // elements per row
+    int pitch;          // elements per stored row (>= nx + 2 * kGhost, multiple of 32)
     long long plane;    // elements per population plane = ny * pitch
     int walls;          // 0 periodic in y, 1 bounce-back walls in y
 };
 
 struct StepLaunch {
-    int tx;             // columns per CTA (threads)
+    int variant;        // compiled (strip width, ring depth) choice, see step_variant_tx
+    int tx;             // lattice columns per CTA (two per thread)
     int rows;           // rows each CTA marches over
+    int ctas_per_sm;    // resident CTAs per SM reported by the occupancy calculator
 };
 
 // ---- kernels (lb_kernels.cu) -------------------------------------------------------
-// All launches go to `stream`; they return cudaGetLastError() of the launch.
+int step_variant_count();
+int step_variant_tx(int variant);
+StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
+                            int rows_override);
+cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l);
+// tensor_map_in: a CUtensorMap describing the input buffer (3-D: x, y, population)
 cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l,
-                        const void *fin, void *fout, int *err, cudaStream_t stream);
+                        const void *tensor_map_in, void *gout, int *err, cudaStream_t stream);
+cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf,
+                            cudaStream_t stream);
+cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f,
+                          cudaStream_t stream);
 cudaError_t launch_init_feq(int prec, const Consts &c, const Geom &g, const double *rho,
                             const double *ux, const double *uy, void *f, int *err,
                             cudaStream_t stream);
-cudaError_t launch_psi_field(int prec, const Consts &c, const Geom &g, const void *f,
-                             double *psi, int *err, cudaStream_t stream);
-cudaError_t launch_macro_fields(int prec, const Consts &c, const Geom &g, const void *f,
-                                const double *psi, double *rho, double *ux, double *uy,
+// psi: nx*ny elements of the storage type
+cudaError_t launch_psi_field(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                             void *psi, int *err, cudaStream_t stream);
+cudaError_t launch_macro_fields(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                const void *psi, double *rho, double *ux, double *uy,
                                 cudaStream_t stream);
 // Deterministic FP64 reduction: partials must hold 4 * reduce_blocks(n) doubles.
 int reduce_blocks(long long n_sites);
-cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const void *f,
-                                const double *psi, double *partials, double *out4,
+cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                const void *psi, double *partials, double *out4,
                                 cudaStream_t stream);
-
-StepLaunch default_step_launch(const Geom &g, int num_sms);
 
 // ---- host thermodynamics (lb_thermo.cpp) ---------------------------------------------
 double p_eos_host(const lb_eos &e, double G, double rho);

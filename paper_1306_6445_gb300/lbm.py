@@ -29,7 +29,8 @@ LB_BC_PERIODIC, LB_BC_WALLS_Y = 0, 1
 EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_u", "lb_step",
             "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
-            "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell"]
+            "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
+            "lb_set_launch", "lb_get_launch", "lb_debug_stall_row"]
 
 
 class LBError(RuntimeError):
@@ -86,6 +87,10 @@ def load_library():
         "lb_free": (None, [P]),
         "lb_cs_critical": (I, [D, D, D, DP, DP]),
         "lb_maxwell": (I, [C.POINTER(c_lb_eos), D, DP, DP, DP]),
+        "lb_launch_variants": (I, []),
+        "lb_set_launch": (I, [P, I, I]),
+        "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+        "lb_debug_stall_row": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,6 +256,25 @@ def lb_steps_done(ctx) -> int:
 
 def lb_kernels_per_step(ctx) -> int:
     return int(load_library().lb_kernels_per_step(ctx))
+
+
+def lb_launch_variants() -> int:
+    return int(load_library().lb_launch_variants())
+
+
+def lb_set_launch(ctx, variant: int, rows: int = 0):
+    _check(load_library().lb_set_launch(ctx, int(variant), int(rows)), "lb_set_launch", ctx)
+
+
+def lb_get_launch(ctx):
+    v, tx, rows, occ = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().lb_get_launch(ctx, C.byref(v), C.byref(tx), C.byref(rows),
+                                        C.byref(occ)), "lb_get_launch")
+    return {"variant": v.value, "tx": tx.value, "rows": rows.value, "ctas_per_sm": occ.value}
+
+
+def lb_debug_stall_row(ctx, row: int):
+    _check(load_library().lb_debug_stall_row(ctx, int(row)), "lb_debug_stall_row", ctx)
 
 
 def lb_status_of(ctx) -> int:

@@ -43,9 +43,10 @@ def test_library_exports_every_declared_symbol(lbm):
 
 
 def test_pitch_and_buffer_size(lbm):
+    # nx + 8 ghost/apron columns, rounded up to 32 elements
     assert lbm.lb_pitch(1, lbm.LB_FP32) == 32
-    assert lbm.lb_pitch(2048, lbm.LB_FP64) == 2048
-    assert lbm.lb_pitch(2049, lbm.LB_FP32) == 2080
+    assert lbm.lb_pitch(2048, lbm.LB_FP64) == 2080
+    assert lbm.lb_pitch(2024, lbm.LB_FP32) == 2048
     assert lbm.lb_buffer_bytes(100, 7, lbm.LB_FP64) == 9 * 7 * 128 * 8
     assert lbm.lb_buffer_bytes(0, 7, lbm.LB_FP64) == 0
 

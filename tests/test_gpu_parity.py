@@ -47,7 +47,7 @@ def case_params(lbm, kind):
     if kind == "cs":
         return lbm.cs_eos(0.8), -1.0, (0.02, 0.31)
     if kind == "exp":
-        return lbm.EOSParams(kind="exp"), -40.0, (80.0, 515.0)
+        return lbm.EOSParams(kind="exp"), -40.0, (150.0, 420.0)
     return lbm.EOSParams(kind="piecewise"), -1.0, (1.0, 100.0)
 
 
@@ -287,4 +287,62 @@ def test_zero_steps_is_a_no_op(lbm):
     a = lat.populations()
     lat.step(0)
     assert np.array_equal(a, lat.populations())
+    lat.close()
+
+
+# --------------------------------------------------------------------------- launch shapes
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_every_launch_variant_gives_identical_bits(lbm, prec):
+    """The per-site arithmetic does not depend on the strip width, ring depth or rows per
+    CTA, so every launch shape must produce the same bits (and match the oracle)."""
+    eos, G, (lo, hi) = case_params(lbm, "cs")
+    rates = lbm.RateParams.from_viscosity(0.1)
+    nx, ny = 301, 77
+    rng = np.random.default_rng(5)
+    rho = I.smooth_random_density(rng, nx, ny, lo, hi)
+    f0 = I.random_populations(rng, rho)
+    results = []
+    for walls in (False, True):
+        shapes = [(v, r) for v in range(lbm.lb_launch_variants()) for r in (0, 8, 13, 77)]
+        outs = []
+        for (v, r) in shapes:
+            lat = lbm.Lattice(nx, ny, eos, G, kappa=0.4, sigma_force=0.05, rates=rates,
+                              prec=prec, walls_y=walls)
+            lbm.lb_set_launch(lat.ctx, v, r)
+            lat.set_populations(f0)
+            lat.step(3)
+            outs.append(lat.populations())
+            lat.close()
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        p = oracle_params(eos, G, 0.4, 0.05, rates, walls)
+        ref = OL.run(f0.astype(prec == "fp32" and np.float32 or np.float64).astype(np.float64), p, 3)
+        tol = 1e-13 if prec == "fp64" else fp32_tol(3)
+        assert rel_err(outs[0], ref) <= tol
+        results.append(outs[0])
+
+
+def test_stalled_wait_times_out_and_poisons(lbm):
+    """A ring row that is never requested makes the bounded mbarrier wait give up after
+    about a second: the step reports LB_ETIMEOUT instead of hanging, and later calls keep
+    returning it."""
+    eos = lbm.EOSParams(kind="exp")
+    rho = I.droplet_density(64, 64, 12.0, 400.0, 150.0)
+    lat = lbm.Lattice(64, 64, eos, -40.0, prec="fp32")
+    lat.set_rho_u(rho)
+    lbm.lb_debug_stall_row(lat.ctx, 20)
+    lat.step(1)
+    with pytest.raises(lbm.LBError) as ei:
+        lat.sync()
+    assert ei.value.status == lbm.LB_ETIMEOUT
+    with pytest.raises(lbm.LBError) as ei:
+        lat.step(1)
+    assert ei.value.status == lbm.LB_ETIMEOUT
+    lat.close()
+    # the device is still usable afterwards
+    lat = lbm.Lattice(16, 16, eos, -40.0, prec="fp32")
+    lat.set_rho_u(np.full((16, 16), 300.0))
+    lat.step(2)
+    assert np.allclose(lat.rho(), 300.0, rtol=1e-6)
     lat.close()
