@@ -160,6 +160,21 @@ lb_status lb_set_populations(lb_ctx *ctx, const void *src, size_t bytes);
  * out[3] = max |v|. Synchronises. LB_ENONFINITE (and poisoning) if any is not finite. */
 lb_status lb_reduce(lb_ctx *ctx, double out[4]);
 
+/* lb_reduce without any device allocation, for callers that cannot allocate: for
+ * example a plugin confined to a device-memory budget given to it by its host
+ * application, or a loop that must not call cudaMalloc/cudaFree because they can
+ * synchronise the whole device. The paper has no counterpart; this is library plumbing.
+ * Same outputs as lb_reduce (out[0] = sum rho, out[1..2] = sum rho v, out[3] = max |v|,
+ * FP64, fixed reduction order), written to the caller's host array; synchronises the
+ * context's stream. Its scratch is one static device array of 4104 doubles (32.8 KB) that
+ * every GPU loading this library holds until the process exits; lattices of at most
+ * 2^24 sites are accepted (LB_EINVAL with a message otherwise). The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture. All calls share the array: calls that overlap on the
+ * GPU (for example on two streams) race and must be serialised by the caller.
+ * Errors: as lb_reduce (LB_EDOMAIN, LB_ENONFINITE poison the context), LB_ECUDA. */
+lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]);
+
 /* Number of time steps taken since lb_set_rho_u. */
 long long lb_steps_done(const lb_ctx *ctx);
 

@@ -287,6 +287,28 @@ lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, doub
 
 }  // namespace
 
+namespace lbm {
+
+lb_status ctx_view(const lb_ctx *c, CtxView *v) {
+    if (!c || !v) return LB_EINVAL;
+    v->g = c->f[c->cur];
+    v->geom = c->geom;
+    v->consts = c->consts;
+    v->prec = c->prec;
+    v->stream = c->stream;
+    v->sticky = c->sticky;
+    return LB_OK;
+}
+
+lb_status ctx_fail(lb_ctx *c, lb_status s, const char *msg, bool poison_ctx) {
+    if (!c) return s;
+    c->msg = msg ? msg : "";
+    if (poison_ctx) c->sticky = s;
+    return s;
+}
+
+}  // namespace lbm
+
 extern "C" {
 
 size_t lb_pitch(int nx, int prec) {

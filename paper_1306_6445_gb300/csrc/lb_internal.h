@@ -76,6 +76,19 @@ cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const 
                                 const void *psi, double *partials, double *out4,
                                 cudaStream_t stream);
 
+// ---- read-only view of a context for entry points outside lb_api.cu (lb_noalloc.cu) ---
+struct CtxView {
+    const void *g;        // device buffer holding the current state
+    Geom geom;
+    Consts consts;
+    int prec;
+    cudaStream_t stream;
+    lb_status sticky;
+};
+lb_status ctx_view(const lb_ctx *c, CtxView *v);
+// record a message; with poison = true also make `s` the context's sticky status
+lb_status ctx_fail(lb_ctx *c, lb_status s, const char *msg, bool poison);
+
 // ---- host thermodynamics (lb_thermo.cpp) ---------------------------------------------
 double p_eos_host(const lb_eos &e, double G, double rho);
 

@@ -30,7 +30,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
-            "lb_set_launch", "lb_get_launch", "lb_debug_stall_row"]
+            "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc"]
 
 
 class LBError(RuntimeError):
@@ -91,6 +91,7 @@ def load_library():
         "lb_set_launch": (I, [P, I, I]),
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
+        "lb_reduce_noalloc": (I, [P, DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +248,13 @@ def lb_set_populations(ctx, src_ptr: int, nbytes: int):
 def lb_reduce(ctx):
     out = np.zeros(4)
     _check(load_library().lb_reduce(ctx, _dp(out)), "lb_reduce", ctx)
+    return out
+
+
+def lb_reduce_noalloc(ctx):
+    """lb_reduce without device allocation (static scratch); see include/lb.h."""
+    out = np.zeros(4)
+    _check(load_library().lb_reduce_noalloc(ctx, _dp(out)), "lb_reduce_noalloc", ctx)
     return out
 
 
