@@ -71,7 +71,8 @@ bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
 lb_status validate(int nx, int ny, const lb_eos *eos, double G, double kappa, double sigma,
                    const lb_rates *r, int prec, int bc, std::string &why) {
     if (nx < 3 || ny < 3) { why = "nx and ny must be >= 3"; return LB_EINVAL; }
-    if ((long long)(nx + 2 * lbm::kGhost + 32) * ny > (1LL << 31) - 1) { why = "lattice too large"; return LB_EINVAL; }
+    // the step kernel addresses a buffer with 32-bit element offsets (9 planes)
+    if (9LL * (long long)lb_pitch(nx, prec) * ny >= (1LL << 32)) { why = "lattice too large"; return LB_EINVAL; }
     if (!eos || !r) { why = "eos and rates must not be NULL"; return LB_EINVAL; }
     if (prec != LB_FP32 && prec != LB_FP64) { why = "prec must be LB_FP64 or LB_FP32"; return LB_EINVAL; }
     if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y) { why = "bad boundary kind"; return LB_EINVAL; }

@@ -133,6 +133,35 @@ __device__ __forceinline__ V2<double> vfma(V2<double> a, V2<double> b, V2<double
     return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
 }
 
+// psi of two densities; lane by lane the same operations, in the same order and with
+// the same rounding, as eos_psi (so a site's psi does not depend on which lane or which
+// kernel computes it). `hi_valid` = false: the second lane is padding and is not checked.
+template <typename T, int EOS>
+__device__ __forceinline__ V2<T> eos_psi2(V2<T> rho, const DevConsts<T> &P, bool hi_valid,
+                                          bool &bad) {
+    if constexpr (EOS == LB_EOS_CS) {
+        using V = V2<T>;
+        const V one = V::all(T(1));
+        const V eta = V::all(P.b4) * rho;
+        const V om = one - eta;
+        const V poly = vfma(eta, vfma(eta, one - eta, one), one);
+        const V num = (rho * V::all(P.RT)) * poly;
+        const V den = (om * om) * om;
+        const V q(lb_div(num.lo(), den.lo()), lb_div(num.hi(), den.hi()));
+        const V p = q - V::all(P.a) * (rho * rho);
+        const V arg = (p - rho * V::all(T(1.0 / 3.0))) * V::all(P.two_over_G);
+        bad |= !(arg.lo() > T(0)) || !(rho.lo() > T(0));
+        if (hi_valid) bad |= !(arg.hi() > T(0)) || !(rho.hi() > T(0));
+        return V(lb_sqrt_pos(arg.lo()), lb_sqrt_pos(arg.hi()));
+    } else {
+        bool b2 = false;
+        const T lo = eos_psi<T, EOS>(rho.lo(), P, bad);
+        const T hi = eos_psi<T, EOS>(rho.hi(), P, b2);
+        if (hi_valid) bad |= b2;
+        return V2<T>(lo, hi);
+    }
+}
+
 // One collision for two sites: f[9] (populations after streaming, pre-collision) and the
 // potential at the sites and their neighbours pn[a] = psi(x + e_a) (pn[0] = psi(x)) give
 // f*[9] in place.

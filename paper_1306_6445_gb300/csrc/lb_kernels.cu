@@ -139,58 +139,70 @@ struct Ring {
     const T *m, *z, *p;
 };
 
-// f of two adjacent sites (ring column c and c+1) pulled from the ring rows.
-template <typename T, bool WALLS, int BW>
-__device__ __forceinline__ void pull_pair(V2<T> (&f)[9], const Ring<T> &r, int c, bool bottom,
-                                          bool top) {
-    auto at = [&](const T *row, int a, int col) { return row[a * BW + col]; };
-    f[0] = V2<T>(at(r.z, 0, c), at(r.z, 0, c + 1));
-    f[1] = V2<T>(at(r.z, 1, c - 1), at(r.z, 1, c));
-    f[3] = V2<T>(at(r.z, 3, c + 1), at(r.z, 3, c + 2));
-    if (WALLS && bottom) {  // sources below row 0 are wall links: bounce back
-        f[2] = V2<T>(at(r.z, 4, c), at(r.z, 4, c + 1));
-        f[5] = V2<T>(at(r.z, 7, c), at(r.z, 7, c + 1));
-        f[6] = V2<T>(at(r.z, 8, c), at(r.z, 8, c + 1));
-    } else {
-        f[2] = V2<T>(at(r.m, 2, c), at(r.m, 2, c + 1));
-        f[5] = V2<T>(at(r.m, 5, c - 1), at(r.m, 5, c));
-        f[6] = V2<T>(at(r.m, 6, c + 1), at(r.m, 6, c + 2));
-    }
-    if (WALLS && top) {
-        f[4] = V2<T>(at(r.z, 2, c), at(r.z, 2, c + 1));
-        f[7] = V2<T>(at(r.z, 5, c), at(r.z, 5, c + 1));
-        f[8] = V2<T>(at(r.z, 6, c), at(r.z, 6, c + 1));
-    } else {
-        f[4] = V2<T>(at(r.p, 4, c), at(r.p, 4, c + 1));
-        f[7] = V2<T>(at(r.p, 7, c + 1), at(r.p, 7, c + 2));
-        f[8] = V2<T>(at(r.p, 8, c - 1), at(r.p, 8, c));
-    }
-}
-
-// density of one site at ring column c
-template <typename T, bool WALLS, int BW>
-__device__ __forceinline__ T pull_rho(const Ring<T> &r, int c, bool bottom, bool top) {
-    auto at = [&](const T *row, int a, int col) { return row[a * BW + col]; };
-    T v[9];
-    v[0] = at(r.z, 0, c);
-    v[1] = at(r.z, 1, c - 1);
-    v[3] = at(r.z, 3, c + 1);
-    if (WALLS && bottom) {
-        v[2] = at(r.z, 4, c); v[5] = at(r.z, 7, c); v[6] = at(r.z, 8, c);
-    } else {
-        v[2] = at(r.m, 2, c); v[5] = at(r.m, 5, c - 1); v[6] = at(r.m, 6, c + 1);
-    }
-    if (WALLS && top) {
-        v[4] = at(r.z, 2, c); v[7] = at(r.z, 5, c); v[8] = at(r.z, 6, c);
-    } else {
-        v[4] = at(r.p, 4, c); v[7] = at(r.p, 7, c + 1); v[8] = at(r.p, 8, c - 1);
-    }
-    return sum9(v);
-}
-
 template <typename T>
 __device__ __forceinline__ V2<T> rho_pair(const V2<T> (&f)[9]) {
     return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+}
+
+// shared-memory layout of k_pull_collide: S ring stages (each rounded up to 128 bytes),
+// the four-row psi ring, then S mbarriers
+template <typename T, int TX, int S>
+__host__ __device__ constexpr size_t step_bar_offset() {
+    return (size_t)S * (((9u * (TX + 8) * sizeof(T)) + 127u) / 128u * 128u) +
+           (((size_t)4 * (TX + 4) * sizeof(T) + 15u) / 16u * 16u);
+}
+template <typename T, int TX, int S>
+__host__ __device__ constexpr size_t step_smem_bytes() {
+    return step_bar_offset<T, TX, S>() + (size_t)S * 8 + 128;   // + room to align the base
+}
+
+template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> { using type = float2; };
+template <>
+struct Vec2Of<double> { using type = double2; };
+
+// an aligned pair of adjacent elements from shared memory
+template <typename T>
+__device__ __forceinline__ V2<T> lds_pair(const T *p) {
+    const typename Vec2Of<T>::type v = *reinterpret_cast<const typename Vec2Of<T>::type *>(p);
+    return V2<T>(v.x, v.y);
+}
+
+// f of two sites at ring columns cA, cB (adjacent c, c+1 for a thread's own pair; the two
+// strip-halo columns for the halo pair) pulled from the ring rows r.m, r.z, r.p (lattice
+// rows Y-1, Y, Y+1); bounce-back at the walls. ADJ: cB == cA + 1 with cA even, so the
+// unshifted populations come in one aligned 2-element load.
+template <typename T, bool WALLS, int BW, bool ADJ>
+__device__ __forceinline__ void pull2(V2<T> (&f)[9], const Ring<T> &r, int cA, int cB,
+                                      bool bottom, bool top) {
+    auto at = [&](const T *row, int a, int col) { return row[a * BW + col]; };
+    auto two = [&](const T *row, int a, int dc) -> V2<T> {
+        if (ADJ && dc == 0) return lds_pair<T>(row + a * BW + cA);
+        return V2<T>(at(row, a, cA + dc), at(row, a, cB + dc));
+    };
+    f[0] = two(r.z, 0, 0);
+    f[1] = two(r.z, 1, -1);
+    f[3] = two(r.z, 3, 1);
+    if (WALLS && bottom) {   // links from below row 0 are wall links: bounce back
+        f[2] = two(r.z, 4, 0);
+        f[5] = two(r.z, 7, 0);
+        f[6] = two(r.z, 8, 0);
+    } else {
+        f[2] = two(r.m, 2, 0);
+        f[5] = two(r.m, 5, -1);
+        f[6] = two(r.m, 6, 1);
+    }
+    if (WALLS && top) {
+        f[4] = two(r.z, 2, 0);
+        f[7] = two(r.z, 5, 0);
+        f[8] = two(r.z, 6, 0);
+    } else {
+        f[4] = two(r.p, 4, 0);
+        f[7] = two(r.p, 7, 1);
+        f[8] = two(r.p, 8, -1);
+    }
 }
 
 template <typename T>
@@ -206,24 +218,28 @@ __device__ __forceinline__ void store_pair<double>(double *p, V2<double> v, bool
     else p[0] = v.x;
 }
 
-// shared-memory layout of k_pull_collide: S ring stages (each rounded up to 128 bytes),
-// the four-row psi ring, then S mbarriers
-template <typename T, int TX, int S>
-__host__ __device__ constexpr size_t step_bar_offset() {
-    return (size_t)S * (((9u * (TX + 8) * sizeof(T)) + 127u) / 128u * 128u) +
-           (((size_t)4 * (TX + 4) * sizeof(T) + 15u) / 16u * 16u);
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
-template <typename T, int TX, int S>
-__host__ __device__ constexpr size_t step_smem_bytes() {
-    return step_bar_offset<T, TX, S>() + (size_t)S * 8 + 128;   // + room to align the base
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// One time step for a strip of TX columns and `rows` lattice rows.
+//
+// The CTA visits its rows in order k = 0 .. n-1, y_k = start + k*dir (dir = +1 for even
+// blockIdx.y, -1 for odd, so that neighbouring row blocks reach their shared apron rows at
+// the same time and the second read hits L2). Lattice row start + (j-2)*dir is the j-th
+// row requested into the ring (slot j mod S); iteration k reads ring rows j = k+2..k+4 to
+// form psi(y_k + dir), then collides row y_k with psi(y_k - 1 .. y_k + 1). After the
+// barrier of iteration k, ring row k+2 is dead and its slot receives row k+2+S, i.e.
+// S-2 iterations ahead of use.
 template <typename T, int EOS, bool WALLS, int TX, int S>
 __global__ void __launch_bounds__(TX / 2)
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<T> P, const int nx, const int ny, const int pitch,
-               const long long plane, const int rows, int *__restrict__ err) {
-    static_assert(S >= 5, "the ring must hold rows y..y+2 while row y+2 is requested a step ahead");
+               const unsigned plane, const int rows, int *__restrict__ err) {
+    static_assert(S >= 5, "the prologue needs ring rows 0..4 in flight");
     static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
     constexpr int NT = TX / 2;
     constexpr int BW = TX + 8;      // ring row: columns x0-4 .. x0+TX+3 -> ring col = x - x0 + 4
@@ -244,123 +260,171 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     const bool act = c0 < w;
     const bool both = c0 + 1 < w;
     const int yb = blockIdx.y * rows;
-    const int ye = min(yb + rows, ny);
-    const int base = yb - 2;              // first ring row
-    const int last = ye + 1;              // last ring row needed
+    const int n = min(yb + rows, ny) - yb;
+    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    const int start = dir > 0 ? yb : yb + n - 1;
+    const int nj = n + 4;                 // ring rows j = 0 .. n+3
     bool bad = false;
 
-    auto slot = [&](int r) { return (r - base) % S; };
-    auto parity = [&](int r) { return (uint32_t)(((r - base) / S) & 1); };
-    auto rowp = [&](int r) -> const T * { return ring + slot(r) * STAGE_ELEMS; };
-    auto issue = [&](int r) {
-        // periodic: wrap the row; walls: rows outside the lattice are zero-filled by the
-        // TMA unit and never read (bounce-back replaces those links)
-        const int gy = WALLS ? r : ((r % ny) + ny) % ny;
-        if (r == P.stall_row) return;   // test hook: the wait for this row must time out
-        uint64_t *b = &bar[slot(r)];
-        mbar_arrive_expect_tx(b, STAGE_BYTES);
-        tma_load_3d(ring + slot(r) * STAGE_ELEMS, &tin, x0, gy, 0, b);
+    // thread 0 requests ring rows in order
+    int ji = 0, si = 0;
+    auto issue_upto = [&](int jmax) {
+        for (; ji <= jmax && ji < nj; ++ji) {
+            const int r = start + (ji - 2) * dir;
+            const uint32_t sl = (uint32_t)si;
+            si = (si + 1 == S) ? 0 : si + 1;
+            if (r == P.stall_row) continue;   // test hook: the wait for this row must time out
+            // periodic: wrap the row; walls: rows outside the lattice are zero-filled by the
+            // TMA unit and never read (bounce-back replaces those links)
+            const int gy = WALLS ? r : ((r % ny) + ny) % ny;
+            mbar_arrive_expect_tx(&bar[sl], STAGE_BYTES);
+            tma_load_3d(ring + sl * STAGE_ELEMS, &tin, x0, gy, 0, &bar[sl]);
+        }
     };
 
-    int next_issue = base;   // next ring row to request (thread 0's view)
     if (t == 0) {
         prefetch_tensormap(&tin);
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (t == 0) {
-        for (; next_issue <= min(base + S - 1, last); ++next_issue) issue(next_issue);
-    }
+    // everything below reads the previous step's output or writes this step's: wait for
+    // the previous grid to complete (programmatic dependent launch), then let the next one
+    // start its own set-up
+    grid_dependency_wait();
+    grid_dependents_launch();
+    if (t == 0) issue_upto(S - 1);
 
-    // psi of lattice row Y into psi-ring slot Y & 3 (walls: rows -1 and ny copy rows 0, ny-1)
-    auto psi_row = [&](int Y, V2<T> *keep) {
-        const int Ye = WALLS ? min(max(Y, 0), ny - 1) : Y;
-        const Ring<T> r{rowp(Ye - 1), rowp(Ye), rowp(Ye + 1)};
-        const bool bottom = WALLS && Ye == 0, top = WALLS && Ye == ny - 1;
+    auto stage = [&](int s) -> const T * { return ring + s * STAGE_ELEMS; };
+
+    // psi of lattice row Y from ring slots (row Y - dir, Y, Y + dir) into psi slot Y & 3,
+    // keeping the pulled populations of the thread's two sites in `keep`. With walls, the
+    // rows -1 and ny take the psi of rows 0 and ny-1 (already in the psi ring).
+    auto psi_row = [&](int Y, int s_back, int s_mid, int s_fwd, V2<T> (&keep)[9]) {
         T *ps = psis + (Y & 3) * RW;
-        if (act) {
-            V2<T> f[9];
-            pull_pair<T, WALLS, BW>(f, r, c0 + 4, bottom, top);
-            const V2<T> rho = rho_pair(f);
-            const T p0 = eos_psi<T, EOS>(rho.lo(), P, bad);
-            const T p1 = both ? eos_psi<T, EOS>(rho.hi(), P, bad) : T(0);
-            ps[c0 + 2] = p0;
-            if (both) ps[c0 + 3] = p1;   // a lone last site leaves the halo slot to thread NT-1
-            if (keep) {
-#pragma unroll
-                for (int a = 0; a < 9; ++a) keep[a] = f[a];
+        if (WALLS && (Y < 0 || Y >= ny)) {
+            const T *src = psis + ((Y < 0 ? 0 : ny - 1) & 3) * RW;
+            if (act) {
+                ps[c0 + 2] = src[c0 + 2];
+                if (both) ps[c0 + 3] = src[c0 + 3];
             }
-        }
-        if (t == 0) ps[1] = eos_psi<T, EOS>(pull_rho<T, WALLS, BW>(r, 3, bottom, top), P, bad);
-        if (t == NT - 1) ps[w + 2] = eos_psi<T, EOS>(pull_rho<T, WALLS, BW>(r, w + 4, bottom, top), P, bad);
-    };
-
-    // prologue: rows base .. base+3 are needed for psi(yb-1), psi(yb) and f(yb)
-    bool tmo = false;
-    for (int r = base; r <= base + 3; ++r) tmo |= !mbar_wait_bounded(&bar[slot(r)], parity(r));
-    V2<T> fc[9], fn[9];
-    if (!tmo) {
-        psi_row(yb - 1, nullptr);
-        psi_row(yb, fc);
-    }
-    int waited = base + 3;
-
-    for (int y = yb; y < ye; ++y) {
-        if (!tmo && y + 2 > waited) {
-            tmo |= !mbar_wait_bounded(&bar[slot(y + 2)], parity(y + 2));
-            waited = y + 2;
-        }
-        if (!tmo) psi_row(y + 1, (y + 1 < ye) ? fn : nullptr);
-        if (__syncthreads_or(tmo)) {
-            // a bounded wait gave up: report, let the copies in flight land, leave
-            if (t == 0) {
-                atomicOr(err, ERR_TIMEOUT);
-                for (int r = waited + 1; r < next_issue; ++r)
-                    (void)mbar_wait_bounded(&bar[slot(r)], parity(r));
+            if (t == NT - 1) {
+                ps[1] = src[1];
+                ps[w + 2] = src[w + 2];
             }
-            __syncthreads();
             return;
         }
-        // the slot of ring row y-2 is free from here on
-        if (t == 0 && next_issue <= last && next_issue <= y - 2 + S) issue(next_issue++);
+        const Ring<T> r = dir > 0 ? Ring<T>{stage(s_back), stage(s_mid), stage(s_fwd)}
+                                  : Ring<T>{stage(s_fwd), stage(s_mid), stage(s_back)};
+        const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
+        if (act) {
+            pull2<T, WALLS, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top);
+            const V2<T> psi = eos_psi2<T, EOS>(rho_pair(keep), P, both, bad);
+            if (both) {
+                store_pair<T>(ps + c0 + 2, psi, true);
+            } else {
+                ps[c0 + 2] = psi.lo();
+            }
+        }
+        if (t == NT - 1) {   // the two halo columns x0-1 and x0+w as one packed pair
+            V2<T> h[9];
+            pull2<T, WALLS, BW, false>(h, r, 3, w + 4, bottom, top);
+            const V2<T> psi = eos_psi2<T, EOS>(rho_pair(h), P, true, bad);
+            ps[1] = psi.lo();
+            ps[w + 2] = psi.hi();
+        }
+    };
+
+    auto inc = [&](int s) { return (s + 1 == S) ? 0 : s + 1; };
+
+    // prologue: ring rows 0..3 give psi(start) (rows 1..3) and psi(start - dir) (rows 0..2)
+    bool tmo = false;
+#pragma unroll 1
+    for (int j = 0; j <= 3; ++j) tmo |= !mbar_wait_bounded(&bar[j], 0u);
+    V2<T> fA[9], fB[9];
+    if (!tmo) {
+        psi_row(start, 1, 2, 3, fA);
+        psi_row(start - dir, 0, 1, 2, fB);
+    }
+    int jw = 4;                                  // next ring row to wait for
+    int sa = 2 % S, sb = 3 % S, sc = 4 % S;      // slots of ring rows k+2, k+3, k+4
+    uint32_t phc = (uint32_t)((4 / S) & 1);      // phase parity of ring row k+4
+
+    auto body = [&](int k, V2<T> (&fc)[9], V2<T> (&fn)[9]) -> bool {
+        const int y = start + k * dir;
+        if (!tmo) {
+            tmo = !mbar_wait_bounded(&bar[sc], phc);
+            jw = k + 5;
+        }
+        if (!tmo) psi_row(y + dir, sa, sb, sc, fn);
+        if (__syncthreads_or(tmo)) return false;
+        if (t == 0) issue_upto(k + 2 + S);     // ring row k+2 is dead: refill its slot
 
         if (act) {
             const T *pm = psis + ((y - 1) & 3) * RW;
             const T *p0 = psis + (y & 3) * RW;
             const T *pp = psis + ((y + 1) & 3) * RW;
             const int c = c0 + 2;
+            const V2<T> m0 = lds_pair<T>(pm + c), z0 = lds_pair<T>(p0 + c), q0 = lds_pair<T>(pp + c);
+            const T mL = pm[c - 1], mR = pm[c + 2], zL = p0[c - 1], zR = p0[c + 2];
+            const T qL = pp[c - 1], qR = pp[c + 2];
             V2<T> pn[9];
-            pn[0] = V2<T>(p0[c], p0[c + 1]);
-            pn[1] = V2<T>(p0[c + 1], p0[c + 2]);
-            pn[2] = V2<T>(pp[c], pp[c + 1]);
-            pn[3] = V2<T>(p0[c - 1], p0[c]);
-            pn[4] = V2<T>(pm[c], pm[c + 1]);
-            pn[5] = V2<T>(pp[c + 1], pp[c + 2]);
-            pn[6] = V2<T>(pp[c - 1], pp[c]);
-            pn[7] = V2<T>(pm[c - 1], pm[c]);
-            pn[8] = V2<T>(pm[c + 1], pm[c + 2]);
+            pn[0] = z0;
+            pn[1] = V2<T>(z0.hi(), zR);
+            pn[2] = q0;
+            pn[3] = V2<T>(zL, z0.lo());
+            pn[4] = m0;
+            pn[5] = V2<T>(q0.hi(), qR);
+            pn[6] = V2<T>(qL, q0.lo());
+            pn[7] = V2<T>(mL, m0.lo());
+            pn[8] = V2<T>(m0.hi(), mR);
             collide_pair<T>(fc, pn, P);
 
             const int x = x0 + c0;
-            T *o = gout + (long long)y * pitch + x + GH;
+            const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) store_pair<T>(o + a * plane, fc[a], both);
+            for (int a = 0; a < 9; ++a) store_pair<T>(gout + (idx + a * plane), fc[a], both);
             // ghost images of columns 0, 1 (right of nx-1) and nx-2, nx-1 (left of 0)
             if (x < 2 || x + 1 >= nx - 2) {
-                T *rowb = gout + (long long)y * pitch;
+                const unsigned rowi = (unsigned)y * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const T v0 = fc[a].lo(), v1 = fc[a].hi();
-                    if (x < 2) rowb[a * plane + nx + GH + x] = v0;
-                    if (both && x + 1 < 2) rowb[a * plane + nx + GH + x + 1] = v1;
-                    if (x >= nx - 2) rowb[a * plane + x - nx + GH] = v0;
-                    if (both && x + 1 >= nx - 2) rowb[a * plane + x + 1 - nx + GH] = v1;
+                    T *rb = gout + (rowi + a * plane);
+                    if (x < 2) rb[nx + GH + x] = v0;
+                    if (both && x + 1 < 2) rb[nx + GH + x + 1] = v1;
+                    if (x >= nx - 2) rb[x - nx + GH] = v0;
+                    if (both && x + 1 >= nx - 2) rb[x + 1 - nx + GH] = v1;
                 }
             }
         }
-#pragma unroll
-        for (int a = 0; a < 9; ++a) fc[a] = fn[a];
+        sa = sb;
+        sb = sc;
+        sc = inc(sc);
+        if (sc == 0) phc ^= 1u;
+        return true;
+    };
+
+    int k = 0;
+    bool ok = !tmo;
+    if (ok) {
+        for (; k + 1 < n; k += 2) {
+            if (!body(k, fA, fB) || !body(k + 1, fB, fA)) { ok = false; break; }
+        }
+        if (ok && k < n) ok = body(k, fA, fB);
+    } else {
+        ok = !__syncthreads_or(true);
+    }
+    if (!ok) {
+        // a bounded wait gave up: report, let the copies in flight land, leave
+        if (t == 0) {
+            atomicOr(err, ERR_TIMEOUT);
+            int s = jw % S;
+            for (int j = jw; j < ji; ++j, s = inc(s))
+                (void)mbar_wait_bounded(&bar[s], (uint32_t)((j / S) & 1));
+        }
+        __syncthreads();
+        return;
     }
     if (bad) atomicOr(err, ERR_DOMAIN);
 }
@@ -600,10 +664,20 @@ cudaError_t step_variant(const Consts &c, const Geom &g, int rows, const CUtenso
     if (configure) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
-    kern<<<grid, TX / 2, smem, st>>>(tin, static_cast<T *>(out), to_dev<T>(c), g.nx, g.ny,
-                                     g.pitch, g.plane, rows, err);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
+    cfg.blockDim = dim3(TX / 2);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    // programmatic dependent launch: this grid's CTAs may start their set-up while the
+    // previous step drains; they wait (griddepcontrol.wait) before touching global memory
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tin, static_cast<T *>(out), to_dev<T>(c), g.nx, g.ny,
+                              g.pitch, (unsigned)g.plane, rows, err);
 }
 
 template <typename T, int TX, int S>
@@ -628,10 +702,10 @@ cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l,
                           const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                           bool configure) {
     switch (l.variant) {
-        case 0: return step_eos<T, 128, 6>(c, g, l.rows, tin, out, err, st, configure);
-        case 1: return step_eos<T, 128, 5>(c, g, l.rows, tin, out, err, st, configure);
-        case 2: return step_eos<T, 240, 6>(c, g, l.rows, tin, out, err, st, configure);
-        case 3: return step_eos<T, 128, 8>(c, g, l.rows, tin, out, err, st, configure);
+        case 0: return step_eos<T, 128, 5>(c, g, l.rows, tin, out, err, st, configure);
+        case 1: return step_eos<T, 128, 6>(c, g, l.rows, tin, out, err, st, configure);
+        case 2: return step_eos<T, 240, 5>(c, g, l.rows, tin, out, err, st, configure);
+        case 3: return step_eos<T, 64, 6>(c, g, l.rows, tin, out, err, st, configure);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -662,10 +736,10 @@ int occupancy_eos(int eos, bool w) {
 template <typename T>
 int occupancy(int variant, int eos, bool w) {
     switch (variant) {
-        case 0: return occupancy_eos<T, 128, 6>(eos, w);
-        case 1: return occupancy_eos<T, 128, 5>(eos, w);
-        case 2: return occupancy_eos<T, 240, 6>(eos, w);
-        case 3: return occupancy_eos<T, 128, 8>(eos, w);
+        case 0: return occupancy_eos<T, 128, 5>(eos, w);
+        case 1: return occupancy_eos<T, 128, 6>(eos, w);
+        case 2: return occupancy_eos<T, 240, 5>(eos, w);
+        case 3: return occupancy_eos<T, 64, 6>(eos, w);
         default: return 0;
     }
 }
@@ -675,7 +749,7 @@ int occupancy(int variant, int eos, bool w) {
 int step_variant_count() { return 4; }
 
 int step_variant_tx(int variant) {
-    static const int tx[] = {128, 128, 240, 128};
+    static const int tx[] = {128, 128, 240, 64};
     return (variant >= 0 && variant < 4) ? tx[variant] : 0;
 }
 
