@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=-1, help="step-kernel variant (-1: library default)")
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
+    ap.add_argument("--batch-steps", type=int, default=10000,
+                    help="time steps of the 512-lattice batched sweep (0: skip it)")
+    ap.add_argument("--batch-lattices", type=int, default=512)
     return ap.parse_args()
 
 
@@ -219,6 +222,82 @@ def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
     return el, bi, bo
 
 
+def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=6):
+    """The batched Laplace-law sweep: n_lat periodic droplet lattices drawn with the given
+    seed (side U{64..512 step 32}, R/side U[0.15, 0.35], T/Tc U[0.65, 0.95], kappa
+    U[0, 0.95], tau_v U[0.6, 1.2]; CS a=1 b=4 R=1, G=-1, sigma_F=0.087, Maxwell initial
+    densities, FP32), `steps` time steps each, in one persistent launch per step replayed
+    from CUDA graphs. Compared with running `sample` of the lattices one by one through
+    lb_step (extrapolated to all), and with FP64 single-lattice runs of `check` small ones
+    (surface tension error, both measured on the GPU by lb_batch_measure)."""
+    import numpy as np
+    draws = inputs.batch_draws(n_lat, seed)
+    descs, rhos = [], []
+    for d in draws:
+        eos = lbm.cs_eos(d["t_over_tc"])
+        rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
+        descs.append(lbm.LatticeDesc(d["side"], d["side"], eos, -1.0, kappa=d["kappa"],
+                                     sigma_force=0.087,
+                                     rates=lbm.RateParams(s_v=1.0 / d["tau_v"])))
+        rhos.append((d["radius"], rl, rv))
+    radii = np.array([r[0] for r in rhos])
+    sites = sum(d.nx * d.ny for d in descs)
+    b = lbm.Batch(descs, prec="fp32")
+    variant, rows = b.autotune(3)
+    for i, (d, (R, rl, rv)) in enumerate(zip(descs, rhos)):
+        b.set_rho_u(i, inputs.droplet_density(d.nx, d.ny, R, rl, rv))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    el = time.perf_counter() - t0
+    meas = b.measure(radii)
+    launch = b.launch()
+    b.close()
+    failed = int(meas[:, 7].sum())
+    # the same lattices one by one (a random sample, extrapolated)
+    rng = np.random.default_rng(seed + 1)
+    pick = rng.choice(n_lat, size=min(sample, n_lat), replace=False)
+    t_seq = 0.0
+    for i in pick:
+        d = descs[i]
+        lat = lbm.Lattice(d.nx, d.ny, d.eos, d.G, kappa=d.kappa, sigma_force=d.sigma_force,
+                          rates=d.rates, prec="fp32")
+        R, rl, rv = rhos[i]
+        lat.set_rho_u(inputs.droplet_density(d.nx, d.ny, R, rl, rv))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat.step(steps)
+        lat.sync()
+        t_seq += time.perf_counter() - t1
+        lat.close()
+    seq_per_lattice = t_seq / len(pick)
+    # surface tension of the FP32 batch against FP64 single-lattice runs (small lattices)
+    small = [i for i in np.argsort([d.nx for d in descs]) if meas[i, 7] == 0][:check]
+    errs = []
+    for i in small:
+        d = descs[i]
+        R, rl, rv = rhos[i]
+        one = lbm.Batch([d], prec="fp64")
+        one.set_rho_u(0, inputs.droplet_density(d.nx, d.ny, R, rl, rv))
+        one.step(steps)
+        th64 = one.measure(np.array([R]))[0, 0]
+        one.close()
+        errs.append(abs(meas[i, 0] - th64) / abs(th64))
+    return {
+        "lattices": n_lat, "steps": steps, "sites": sites, "failed": failed,
+        "seconds": round(el, 4),
+        "droplets_per_s": round(n_lat / el, 2),
+        "mlups": round(sites * steps / el / 1e6, 1),
+        "sequential_droplets_per_s": round(1.0 / seq_per_lattice, 2),
+        "speedup_vs_sequential": round(seq_per_lattice * n_lat / el, 2),
+        "sigma_rel_err_vs_fp64_max": round(float(max(errs)), 6) if errs else None,
+        "sigma_err_sample": len(errs),
+        "launch": launch, "autotuned": {"variant": variant, "rows": rows},
+        "theta_median": float(np.median(meas[meas[:, 7] == 0, 0])) if failed < n_lat else None,
+    }
+
+
 def cpu_baseline(nx, ny, budget_s=20.0):
     """The FP64 numpy oracle, single thread, on the same droplet lattice: as many whole
     steps as fit in ~budget_s (at least one). Runs in a child process so the BLAS thread
@@ -310,6 +389,9 @@ def native(args):
         e2e = {"value": round(world * sites * inner * K / el / 1e6, 1), "unit": "MLUPS",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
+    batched = None
+    if args.batch_steps > 0:
+        batched = batched_sweep(lbm, torch, inputs, args.batch_lattices, args.batch_steps)
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(nx, ny)
         line = {
@@ -321,7 +403,7 @@ def native(args):
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"},
             "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(),
+            "gpu_launches": launches, "clocks": clocks.summary(), "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -191,6 +191,81 @@ lb_status lb_status_of(const lb_ctx *ctx);
 void lb_free(lb_ctx *ctx);
 
 /* ---------------------------------------------------------------------------------
+ * Batched lattices: many independent periodic lattices of uneven size and parameters
+ * (for example a sweep of droplets over temperature, kappa and viscosity) advanced
+ * together. Each time step is ONE launch of a persistent kernel whose CTAs walk a fixed
+ * list of work items (lattice, strip, row block); runs of 64 steps are captured once in a
+ * CUDA graph and replayed. The update of each lattice is the one of lb_step (Eqs. 4-8,
+ * 17-19), bit for bit. All lattices share the precision and the EOS kind.
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+    int nx, ny;                        /* lattice size, each >= 3 (periodic in x and y) */
+    lb_eos eos;                        /* same kind for every lattice of a batch */
+    double G, kappa, sigma_force;      /* as in lb_init */
+    lb_rates rates;
+} lb_lattice_desc;
+
+typedef struct lb_batch lb_batch;
+
+/* How a lattice of width nx is cut into strips of at most tx columns (tx a multiple of 4)
+ * for the batched step: ceil(nx/tx) strips whose widths differ by at most 7 and all start
+ * on a multiple of 4 columns (only the last width may be any size). Writes the widths and
+ * returns the strip count, or -1 for bad arguments or too small a `widths` array. Host only. */
+int lb_strip_widths(int nx, int tx, int *widths, int max_strips);
+
+/* Create a batch of n lattices (device memory for all populations in one allocation).
+ * Errors: LB_EINVAL (mixed EOS kinds or any argument lb_init would reject), LB_ENOMEM,
+ * LB_ECUDA. The populations start at zero: set every lattice with lb_batch_set_rho_u. */
+lb_status lb_batch_create(lb_batch **out, int n, const lb_lattice_desc *descs, int prec,
+                          void *stream);
+
+/* f = f_eq(rho, u) (Eq. 3) for lattice i from host arrays of nx*ny doubles, [y][x].
+ * Synchronises. Errors: LB_EINVAL, LB_EDOMAIN (psi not real at some site), LB_ECUDA. */
+lb_status lb_batch_set_rho_u(lb_batch *b, int i, const double *rho, const double *ux,
+                             const double *uy);
+
+/* Advance every lattice n >= 0 time steps (queued; returns without waiting). */
+lb_status lb_batch_step(lb_batch *b, int n);
+
+/* Wait for queued work. LB_ETIMEOUT (and poisoning) if a bounded device wait gave up;
+ * per-lattice psi-domain errors do not stop the batch (see lb_batch_errors). */
+lb_status lb_batch_sync(lb_batch *b);
+
+/* Per-lattice error bits (1 = psi domain left, 2 = wait timed out) into flags[n]. */
+lb_status lb_batch_errors(lb_batch *b, int *flags);
+
+/* Density of lattice i (Eq. 6) into a host array of nx*ny doubles. Synchronises. */
+lb_status lb_batch_get_rho(lb_batch *b, int i, double *rho);
+
+/* Populations of lattice i ([alpha][y][x], 9*ny*nx elements of the storage type; `bytes`
+ * must match). Synchronises. */
+lb_status lb_batch_get_populations(lb_batch *b, int i, void *dst, size_t bytes);
+
+/* Laplace-law measurement of every lattice on the GPU (FP64 sums in a fixed order).
+ * radius[i]: nominal droplet radius of lattice i (droplet centred at ((nx-1)/2, (ny-1)/2)).
+ * Writes 8 doubles per lattice: out[8i + 0] = theta = (p_in - p_out) R (Laplace law,
+ * Sec. V.A), 1 = rho_in (mean over r < R/2), 2 = rho_out (mean over r > R + 0.3 min(nx,ny)/2),
+ * 3 = R from the mass, 4 = p_in, 5 = p_out (p = rho/3 + G psi^2/2, the bulk part of
+ * Eq. 20), 6 = total mass, 7 = 1 if the lattice failed (non-finite, psi domain), else 0.
+ * Synchronises. */
+lb_status lb_batch_measure(lb_batch *b, const double *radius, double *out);
+
+/* Time a few steps of every compiled variant and rows-per-item choice on this batch and
+ * keep the fastest; it leaves all populations zeroed and the step count at 0, so call it
+ * before lb_batch_set_rho_u. Writes the choice if the pointers are not NULL. */
+lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *rows);
+
+/* Choose the variant and rows per work item directly; report the current launch. */
+lb_status lb_batch_set_launch(lb_batch *b, int variant, int rows);
+lb_status lb_batch_get_launch(const lb_batch *b, int *variant, int *rows, int *grid,
+                              int *items);
+
+long long lb_batch_steps_done(const lb_batch *b);
+int lb_batch_size(const lb_batch *b);
+const char *lb_batch_last_error(const lb_batch *b);
+void lb_batch_free(lb_batch *b);
+
+/* ---------------------------------------------------------------------------------
  * Host-side thermodynamic set-up helpers (no GPU work). They give the Carnahan-
  * Starling critical point and the Maxwell coexistence densities used to build
  * initial droplets (Sec. II; the Maxwell rule is equal area in 1/rho).

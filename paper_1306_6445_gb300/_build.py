@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblb_gb300.so")
-SOURCES = ["lb_api.cu", "lb_kernels.cu", "lb_thermo.cpp", "lb_noalloc.cu"]
+SOURCES = ["lb_api.cu", "lb_kernels.cu", "lb_thermo.cpp", "lb_noalloc.cu", "lb_batch.cu"]
 HEADERS = ["lb_internal.h", "lb_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",

@@ -27,6 +27,15 @@ struct DevConsts {
     int stall_row;
 };
 
+// Per-lattice record of the batched step (lives in a device table).
+template <typename T>
+struct BatchLattice {
+    T *g[2];              // the lattice's two population buffers
+    DevConsts<T> P;
+    int nx, ny, pitch;
+    unsigned plane;
+};
+
 template <typename T>
 inline DevConsts<T> to_dev(const Consts &c) {
     DevConsts<T> d;

@@ -41,6 +41,13 @@ struct Geom {
     int walls;          // 0 periodic in y, 1 bounce-back walls in y
 };
 
+// One work item of the batched step: a strip of one lattice.
+struct BatchItem {
+    int lat;            // lattice index
+    int x0, w;          // first column (a multiple of 4) and width (<= the kernel's TX)
+    int yb, n, dir;     // first row, row count, march direction (+1 / -1)
+};
+
 struct StepLaunch {
     int variant;        // compiled (strip width, ring depth) choice, see step_variant_tx
     int tx;             // lattice columns per CTA (two per thread)
@@ -75,6 +82,17 @@ int reduce_blocks(long long n_sites);
 cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const void *gbuf,
                                 const void *psi, double *partials, double *out4,
                                 cudaStream_t stream);
+
+// ---- batched step (lb_kernels.cu) --------------------------------------------------------
+// maps: 2 CUtensorMap per lattice (buffer 0, buffer 1); lats: BatchLattice<T> table
+cudaError_t configure_batch(int prec, int eos_kind, int variant, int *ctas_per_sm);
+cudaError_t launch_batch_step(int prec, int eos_kind, int variant, int grid, const void *maps,
+                              const void *lats, const BatchItem *items, int n_items, int phase,
+                              int *errs, cudaStream_t stream);
+// per lattice: out[8*i ..] = mass, sum rho (r < R/2), count, sum rho (outside), count,
+// sum p (inside), sum p (outside), non-finite count; FP64, fixed order
+cudaError_t launch_batch_measure(int prec, int eos_kind, const void *lats, int n_lat, int phase,
+                                 const double *radius, double *out, cudaStream_t stream);
 
 // ---- read-only view of a context for entry points outside lb_api.cu (lb_noalloc.cu) ---
 struct CtxView {

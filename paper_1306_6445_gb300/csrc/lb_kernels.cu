@@ -46,6 +46,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -225,20 +229,24 @@ __device__ __forceinline__ void grid_dependents_launch() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// One time step for a strip of TX columns and `rows` lattice rows.
+// One time step for one strip of a lattice: columns x0 .. x0+w-1 (w <= TX, x0 a multiple of
+// 4) and rows yb .. yb+n-1, visited in order k = 0 .. n-1, y_k = start + k*dir. In the
+// single-lattice kernel dir = +1 for even blockIdx.y and -1 for odd, so that neighbouring
+// row blocks reach their shared apron rows at the same time and the second read hits L2.
+// Lattice row start + (j-2)*dir is the j-th row requested into the ring (slot j mod S);
+// iteration k reads ring rows j = k+2..k+4 to form psi(y_k + dir), then collides row y_k
+// with psi(y_k - 1 .. y_k + 1). After the barrier of iteration k, ring row k+2 is dead and
+// its slot receives row k+2+S, i.e. S-2 iterations ahead of use.
 //
-// The CTA visits its rows in order k = 0 .. n-1, y_k = start + k*dir (dir = +1 for even
-// blockIdx.y, -1 for odd, so that neighbouring row blocks reach their shared apron rows at
-// the same time and the second read hits L2). Lattice row start + (j-2)*dir is the j-th
-// row requested into the ring (slot j mod S); iteration k reads ring rows j = k+2..k+4 to
-// form psi(y_k + dir), then collides row y_k with psi(y_k - 1 .. y_k + 1). After the
-// barrier of iteration k, ring row k+2 is dead and its slot receives row k+2+S, i.e.
-// S-2 iterations ahead of use.
+// The caller has initialised the S ring mbarriers (fresh, phase 0) and waited for the
+// previous grid. Returns 0, or ERR_TIMEOUT after a bounded wait gave up (then every copy
+// still in flight has landed, or its own bounded wait gave up too).
 template <typename T, int EOS, bool WALLS, int TX, int S>
-__global__ void __launch_bounds__(TX / 2)
-k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
-               const DevConsts<T> P, const int nx, const int ny, const int pitch,
-               const unsigned plane, const int rows, int *__restrict__ err) {
+__device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ gout,
+                                     const DevConsts<T> &P, const int nx, const int ny,
+                                     const int pitch, const unsigned plane, const int x0,
+                                     const int w, const int yb, const int n, const int dir,
+                                     unsigned char *smem_raw, bool &bad) {
     static_assert(S >= 5, "the prologue needs ring rows 0..4 in flight");
     static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
     constexpr int NT = TX / 2;
@@ -246,25 +254,16 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     constexpr int RW = TX + 4;      // psi row: columns x0-2 .. x0+TX+1 -> psi col = x - x0 + 2
     constexpr uint32_t STAGE_BYTES = 9u * BW * sizeof(T);
     constexpr int STAGE_ELEMS = (int)(((STAGE_BYTES + 127u) / 128u) * 128u / sizeof(T));
-    extern __shared__ __align__(128) unsigned char smem_dyn[];
-    // the TMA destinations are placed on 128-byte boundaries of the shared window
-    unsigned char *smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     T *ring = reinterpret_cast<T *>(smem_raw);                 // S stages, 128-byte aligned
     T *psis = ring + S * STAGE_ELEMS;                           // [4][RW]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>());
 
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * TX;
-    const int w = min(TX, nx - x0);
     const int c0 = 2 * t;                 // first of the thread's two columns, relative to x0
     const bool act = c0 < w;
     const bool both = c0 + 1 < w;
-    const int yb = blockIdx.y * rows;
-    const int n = min(yb + rows, ny) - yb;
-    const int dir = (blockIdx.y & 1) ? -1 : 1;
     const int start = dir > 0 ? yb : yb + n - 1;
     const int nj = n + 4;                 // ring rows j = 0 .. n+3
-    bool bad = false;
 
     // thread 0 requests ring rows in order
     int ji = 0, si = 0;
@@ -278,21 +277,10 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
             // TMA unit and never read (bounce-back replaces those links)
             const int gy = WALLS ? r : ((r % ny) + ny) % ny;
             mbar_arrive_expect_tx(&bar[sl], STAGE_BYTES);
-            tma_load_3d(ring + sl * STAGE_ELEMS, &tin, x0, gy, 0, &bar[sl]);
+            tma_load_3d(ring + sl * STAGE_ELEMS, tmap, x0, gy, 0, &bar[sl]);
         }
     };
 
-    if (t == 0) {
-        prefetch_tensormap(&tin);
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    // everything below reads the previous step's output or writes this step's: wait for
-    // the previous grid to complete (programmatic dependent launch), then let the next one
-    // start its own set-up
-    grid_dependency_wait();
-    grid_dependents_launch();
     if (t == 0) issue_upto(S - 1);
 
     auto stage = [&](int s) -> const T * { return ring + s * STAGE_ELEMS; };
@@ -416,17 +404,93 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
         ok = !__syncthreads_or(true);
     }
     if (!ok) {
-        // a bounded wait gave up: report, let the copies in flight land, leave
+        // a bounded wait gave up: let the copies in flight land (each wait bounded), leave
         if (t == 0) {
-            atomicOr(err, ERR_TIMEOUT);
             int s = jw % S;
             for (int j = jw; j < ji; ++j, s = inc(s))
                 (void)mbar_wait_bounded(&bar[s], (uint32_t)((j / S) & 1));
         }
         __syncthreads();
-        return;
+        return ERR_TIMEOUT;
     }
+    return 0;
+}
+
+__device__ __forceinline__ unsigned char *align_smem128(unsigned char *p) {
+    return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
+template <int S>
+__device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            if (reuse) mbar_inval(&bar[s]);
+            mbar_init(&bar[s], 1);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
+template <typename T, int EOS, bool WALLS, int TX, int S>
+__global__ void __launch_bounds__(TX / 2)
+k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
+               const DevConsts<T> P, const int nx, const int ny, const int pitch,
+               const unsigned plane, const int rows, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    if (threadIdx.x == 0) prefetch_tensormap(&tin);
+    init_ring_barriers<S>(reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>()),
+                          false);
+    // everything below reads the previous step's output or writes this step's: wait for
+    // the previous grid to complete (programmatic dependent launch), then let the next one
+    // start its own set-up
+    grid_dependency_wait();
+    grid_dependents_launch();
+    const int x0 = blockIdx.x * TX;
+    const int yb = blockIdx.y * rows;
+    bool bad = false;
+    const int st = march<T, EOS, WALLS, TX, S>(&tin, gout, P, nx, ny, pitch, plane, x0,
+                                               min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
+                                               (blockIdx.y & 1) ? -1 : 1, smem_raw, bad);
+    if (threadIdx.x == 0 && st) atomicOr(err, st);
     if (bad) atomicOr(err, ERR_DOMAIN);
+}
+
+// Many lattices (periodic) in one launch: a persistent grid walks a fixed list of work
+// items (lattice, strip, row block), item i going to CTA i mod gridDim.x. Per-lattice
+// constants, buffers and TMA descriptors come from device tables; `phase` says which of a
+// lattice's two buffers holds the current state. Errors are recorded per lattice.
+template <typename T, int EOS, int TX, int S>
+__global__ void __launch_bounds__(TX / 2)
+k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
+             const BatchItem *__restrict__ items, const int n_items, const int phase,
+             int *__restrict__ errs) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>());
+    init_ring_barriers<S>(bar, false);
+    grid_dependency_wait();
+    grid_dependents_launch();
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const BatchItem it = items[i];
+        const BatchLattice<T> &L = lats[it.lat];
+        const DevConsts<T> P = L.P;
+        const CUtensorMap *map = maps + 2 * it.lat + phase;
+        if (threadIdx.x == 0) prefetch_tensormap(map);
+        bool bad = false;
+        const int st = march<T, EOS, false, TX, S>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
+                                                   L.plane, it.x0, it.w, it.yb, it.n, it.dir,
+                                                   smem_raw, bad);
+        if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
+        if (st) {
+            if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
+            return;   // the ring is in an unknown state: this CTA stops
+        }
+        __syncthreads();                 // every thread is done with the ring of this item
+        init_ring_barriers<S>(bar, true);
+    }
 }
 
 // ---------------------------------------------------------------- permutations
@@ -744,6 +808,106 @@ int occupancy(int variant, int eos, bool w) {
     }
 }
 
+// Per-lattice Laplace sums for the batched sweep: one CTA per lattice, fixed per-thread
+// order and fixed tree (deterministic). Inside: r < R/2; outside: r > R + 0.3 min(nx,ny)/2,
+// around the lattice centre ((nx-1)/2, (ny-1)/2); p = rho/3 + (G/2) psi^2.
+template <typename T, int EOS>
+__global__ void __launch_bounds__(RED_THREADS)
+k_batch_measure(const BatchLattice<T> *__restrict__ lats, int phase,
+                const double *__restrict__ radius, double *__restrict__ out) {
+    __shared__ double s[8][RED_THREADS];
+    const BatchLattice<T> &L = lats[blockIdx.x];
+    const DevConsts<T> P = L.P;
+    const int nx = L.nx, ny = L.ny;
+    const T *g = L.g[phase];
+    const double R = radius[blockIdx.x];
+    const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1);
+    const double r_in = 0.5 * R, r_out = R + 0.3 * 0.5 * min(nx, ny);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long n = (long long)nx * ny;
+    for (long long i = threadIdx.x; i < n; i += RED_THREADS) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        T v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+            v[a] = pull_global<T, false>(g, a, x, y, nx, ny, L.pitch, (long long)L.plane);
+        const T rho = sum9(v);
+        bool bad = false;
+        const T psi = eos_psi<T, EOS>(rho, P, bad);
+        const double dr = double(rho);
+        const double p = dr / 3.0 + 0.5 * double(P.G) * double(psi) * double(psi);
+        acc[0] += dr;
+        const double r = sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy));
+        if (r < r_in) { acc[1] += dr; acc[2] += 1; acc[5] += p; }
+        if (r > r_out) { acc[3] += dr; acc[4] += 1; acc[6] += p; }
+        if (bad || !(dr == dr) || !(p == p)) acc[7] += 1;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int wdt = RED_THREADS / 2; wdt > 0; wdt >>= 1) {
+        if (threadIdx.x < wdt) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + wdt];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) out[blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+template <typename T, int EOS, int TX, int S>
+cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void *maps,
+                          const void *lats, const BatchItem *items, int n_items, int phase,
+                          int *errs, cudaStream_t st) {
+    auto kern = k_batch_step<T, EOS, TX, S>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S>();
+    if (configure) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, TX / 2, smem);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TX / 2);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const CUtensorMap *>(maps),
+                              static_cast<const BatchLattice<T> *>(lats), items, n_items, phase,
+                              errs);
+}
+
+template <typename T, int TX, int S>
+cudaError_t batch_eos(int eos, bool configure, int *occ, int grid, const void *maps,
+                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
+                      cudaStream_t st) {
+    switch (eos) {
+        case LB_EOS_CS:
+            return batch_variant<T, LB_EOS_CS, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case LB_EOS_EXP:
+            return batch_variant<T, LB_EOS_EXP, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        default:
+            return batch_variant<T, LB_EOS_PIECEWISE, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+    }
+}
+
+template <typename T>
+cudaError_t batch_dispatch(int variant, int eos, bool configure, int *occ, int grid,
+                           const void *maps, const void *lats, const BatchItem *items,
+                           int n_items, int phase, int *errs, cudaStream_t st) {
+    switch (variant) {
+        case 0: return batch_eos<T, 128, 5>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 1: return batch_eos<T, 128, 6>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 2: return batch_eos<T, 240, 5>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 3: return batch_eos<T, 64, 6>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 int step_variant_count() { return 4; }
@@ -902,6 +1066,46 @@ cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, RED_THREADS, 0, st>>>(partials, nb, out4);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+namespace lbm {
+
+cudaError_t configure_batch(int prec, int eos_kind, int variant, int *ctas_per_sm) {
+    if (prec == LB_FP32)
+        return batch_dispatch<float>(variant, eos_kind, true, ctas_per_sm, 0, nullptr, nullptr,
+                                     nullptr, 0, 0, nullptr, nullptr);
+    return batch_dispatch<double>(variant, eos_kind, true, ctas_per_sm, 0, nullptr, nullptr,
+                                  nullptr, 0, 0, nullptr, nullptr);
+}
+
+cudaError_t launch_batch_step(int prec, int eos_kind, int variant, int grid, const void *maps,
+                              const void *lats, const BatchItem *items, int n_items, int phase,
+                              int *errs, cudaStream_t st) {
+    if (prec == LB_FP32)
+        return batch_dispatch<float>(variant, eos_kind, false, nullptr, grid, maps, lats, items,
+                                     n_items, phase, errs, st);
+    return batch_dispatch<double>(variant, eos_kind, false, nullptr, grid, maps, lats, items,
+                                  n_items, phase, errs, st);
+}
+
+cudaError_t launch_batch_measure(int prec, int eos_kind, const void *lats, int n_lat, int phase,
+                                 const double *radius, double *out, cudaStream_t st) {
+#define LB_BM(T, EOSK)                                                                         \
+    k_batch_measure<T, EOSK><<<n_lat, RED_THREADS, 0, st>>>(                                   \
+        static_cast<const BatchLattice<T> *>(lats), phase, radius, out)
+    if (prec == LB_FP32) {
+        if (eos_kind == LB_EOS_CS) LB_BM(float, LB_EOS_CS);
+        else if (eos_kind == LB_EOS_EXP) LB_BM(float, LB_EOS_EXP);
+        else LB_BM(float, LB_EOS_PIECEWISE);
+    } else {
+        if (eos_kind == LB_EOS_CS) LB_BM(double, LB_EOS_CS);
+        else if (eos_kind == LB_EOS_EXP) LB_BM(double, LB_EOS_EXP);
+        else LB_BM(double, LB_EOS_PIECEWISE);
+    }
+#undef LB_BM
     return cudaGetLastError();
 }
 

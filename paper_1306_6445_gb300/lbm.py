@@ -30,7 +30,12 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
-            "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc"]
+            "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
+            "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
+            "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
+            "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
+            "lb_batch_steps_done", "lb_batch_size", "lb_batch_last_error", "lb_batch_free",
+            "lb_strip_widths"]
 
 
 class LBError(RuntimeError):
@@ -49,6 +54,11 @@ class c_lb_eos(C.Structure):
 class c_lb_rates(C.Structure):
     _fields_ = [("s_rho", C.c_double), ("s_e", C.c_double), ("s_zeta", C.c_double),
                 ("s_j", C.c_double), ("s_q", C.c_double), ("s_v", C.c_double)]
+
+
+class c_lb_lattice_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("eos", c_lb_eos), ("G", C.c_double),
+                ("kappa", C.c_double), ("sigma_force", C.c_double), ("rates", c_lb_rates)]
 
 
 _lib = None
@@ -92,6 +102,22 @@ def load_library():
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
         "lb_reduce_noalloc": (I, [P, DP]),
+        "lb_batch_create": (I, [C.POINTER(P), I, C.POINTER(c_lb_lattice_desc), I, P]),
+        "lb_batch_set_rho_u": (I, [P, I, DP, DP, DP]),
+        "lb_batch_step": (I, [P, I]),
+        "lb_batch_sync": (I, [P]),
+        "lb_batch_errors": (I, [P, C.POINTER(I)]),
+        "lb_batch_get_rho": (I, [P, I, DP]),
+        "lb_batch_get_populations": (I, [P, I, P, SZ]),
+        "lb_batch_measure": (I, [P, DP, DP]),
+        "lb_batch_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
+        "lb_batch_set_launch": (I, [P, I, I]),
+        "lb_batch_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+        "lb_batch_steps_done": (C.c_longlong, [P]),
+        "lb_batch_size": (I, [P]),
+        "lb_batch_last_error": (C.c_char_p, [P]),
+        "lb_batch_free": (None, [P]),
+        "lb_strip_widths": (I, [I, I, C.POINTER(I), I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -382,6 +408,136 @@ class Lattice:
             lb_free(self.ctx)
             self.ctx = None
         self._tensors = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------
+# batched lattices
+# ------------------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class LatticeDesc:
+    """One lattice of a batch (periodic): size and parameters as in lb_init."""
+
+    nx: int
+    ny: int
+    eos: EOSParams
+    G: float
+    kappa: float = 0.0
+    sigma_force: float = 0.0
+    rates: RateParams = field(default_factory=RateParams)
+
+    def to_c(self) -> c_lb_lattice_desc:
+        return c_lb_lattice_desc(self.nx, self.ny, self.eos.to_c(), self.G, self.kappa,
+                                 self.sigma_force, self.rates.to_c())
+
+
+def _bcheck(status: int, where: str, b=None):
+    if status != LB_OK:
+        msg = ""
+        if b is not None:
+            raw = load_library().lb_batch_last_error(b)
+            msg = raw.decode() if raw else ""
+        raise LBError(status, where, msg)
+
+
+def lb_strip_widths(nx: int, tx: int):
+    out = (C.c_int * 4096)()
+    n = load_library().lb_strip_widths(nx, tx, out, 4096)
+    if n < 0:
+        raise LBError(LB_EINVAL, "lb_strip_widths")
+    return list(out[:n])
+
+
+class Batch:
+    """Many periodic lattices advanced together (lb_batch_*), on torch's current stream."""
+
+    def __init__(self, descs, prec: str = "fp32", stream=None):
+        lib = load_library()
+        self.descs = list(descs)
+        self.n = len(self.descs)
+        self._prec = LB_FP32 if prec == "fp32" else LB_FP64
+        self.dtype = np.float32 if self._prec == LB_FP32 else np.float64
+        arr = (c_lb_lattice_desc * self.n)(*[d.to_c() for d in self.descs])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.b = C.c_void_p()
+        _bcheck(lib.lb_batch_create(C.byref(self.b), self.n, arr, self._prec, stream),
+                "lb_batch_create")
+
+    def set_rho_u(self, i, rho, ux=None, uy=None):
+        d = self.descs[i]
+        z = np.zeros((d.ny, d.nx))
+        rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64)
+                       for a in (rho, z if ux is None else ux, z if uy is None else uy))
+        _bcheck(load_library().lb_batch_set_rho_u(self.b, i, _dp(rho), _dp(ux), _dp(uy)),
+                "lb_batch_set_rho_u", self.b)
+
+    def step(self, n: int):
+        _bcheck(load_library().lb_batch_step(self.b, int(n)), "lb_batch_step", self.b)
+
+    def sync(self):
+        _bcheck(load_library().lb_batch_sync(self.b), "lb_batch_sync", self.b)
+
+    def errors(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int32)
+        st = load_library().lb_batch_errors(self.b, out.ctypes.data_as(C.POINTER(C.c_int)))
+        if st not in (LB_OK, LB_ETIMEOUT):
+            _bcheck(st, "lb_batch_errors", self.b)
+        return out
+
+    def rho(self, i) -> np.ndarray:
+        d = self.descs[i]
+        out = np.empty((d.ny, d.nx))
+        _bcheck(load_library().lb_batch_get_rho(self.b, i, _dp(out)), "lb_batch_get_rho", self.b)
+        return out
+
+    def populations(self, i) -> np.ndarray:
+        d = self.descs[i]
+        out = np.empty((9, d.ny, d.nx), dtype=self.dtype)
+        _bcheck(load_library().lb_batch_get_populations(self.b, i, C.c_void_p(out.ctypes.data),
+                                                        out.nbytes),
+                "lb_batch_get_populations", self.b)
+        return out
+
+    def measure(self, radius) -> np.ndarray:
+        """Per lattice: theta, rho_in, rho_out, R, p_in, p_out, mass, failed (n x 8)."""
+        r = np.ascontiguousarray(radius, dtype=np.float64)
+        out = np.zeros((self.n, 8))
+        _bcheck(load_library().lb_batch_measure(self.b, _dp(r), _dp(out)), "lb_batch_measure",
+                self.b)
+        return out
+
+    def autotune(self, trial_steps: int = 4):
+        v, r = C.c_int(), C.c_int()
+        _bcheck(load_library().lb_batch_autotune(self.b, trial_steps, C.byref(v), C.byref(r)),
+                "lb_batch_autotune", self.b)
+        return v.value, r.value
+
+    def set_launch(self, variant: int, rows: int):
+        _bcheck(load_library().lb_batch_set_launch(self.b, variant, rows), "lb_batch_set_launch",
+                self.b)
+
+    def launch(self):
+        v, r, g, n = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _bcheck(load_library().lb_batch_get_launch(self.b, C.byref(v), C.byref(r), C.byref(g),
+                                                   C.byref(n)), "lb_batch_get_launch")
+        return {"variant": v.value, "rows": r.value, "grid": g.value, "items": n.value}
+
+    @property
+    def steps_done(self) -> int:
+        return int(load_library().lb_batch_steps_done(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load_library().lb_batch_free(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -102,3 +102,20 @@ def test_binding_fails_loudly_without_the_library(lbm, monkeypatch, tmp_path):
     monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="CUDA library missing"):
         lbm.load_library()
+
+
+def test_strip_widths_start_on_16_byte_boundaries(lbm):
+    """The batched step's TMA boxes start at each strip's first column, which must be a
+    multiple of 4 (16 bytes of FP32): every strip but the last is a whole number of 4-column
+    groups, widths fit the kernel's strip and add up to nx."""
+    for tx in (64, 128, 240):
+        for nx in list(range(1, 700)) + [1021, 2048, 4097]:
+            w = lbm.lb_strip_widths(nx, tx)
+            assert len(w) == -(-nx // tx)
+            assert sum(w) == nx
+            assert all(1 <= v <= tx for v in w)
+            assert max(w) - min(w) <= 7          # whole 4-column groups; the last may be partial
+            starts = [sum(w[:k]) for k in range(len(w))]
+            assert all(s % 4 == 0 for s in starts)
+    with pytest.raises(lbm.LBError):
+        lbm.lb_strip_widths(100, 130)      # strip width not a multiple of 4
