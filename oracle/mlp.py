@@ -4,9 +4,9 @@ training and inference kernels.
 Test infrastructure only (see ``oracle/__init__``).
 
 Network (the surrogate of the batched Laplace sweep): inputs (T/T_c, kappa, tau_v),
-outputs (theta, rho_l, rho_v). The inputs are standardised with given means / scales;
-the outputs are learnt in the space (log theta, rho_l, log rho_v), standardised the same
-way. Two hidden layers of width 64 with GELU, GELU(x) = x Phi(x) = x/2 (1 + erf(x/sqrt 2)).
+outputs (theta, rho_l, rho_v). The inputs enter as the features
+(ln(1 - T/T_c), ln(1 - kappa), tau_v), standardised with given means / scales; the outputs
+are learnt in the space (log theta, rho_l, log rho_v), standardised the same way. Two hidden layers of width 64 with GELU, GELU(x) = x Phi(x) = x/2 (1 + erf(x/sqrt 2)).
 Weights are used as BF16 (round to nearest even of the FP32 master copy), activations
 and sums in FP64 here (FP32 on the GPU).
 
@@ -58,6 +58,12 @@ def gelu_grad(z):
     return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
 
 
+def features(x):
+    """(T/T_c, kappa, tau_v) -> (ln(1 - T/T_c), ln(1 - kappa), tau_v)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.stack([np.log1p(-x[:, 0]), np.log1p(-x[:, 1]), x[:, 2]], axis=1)
+
+
 def to_net_targets(y):
     """(theta, rho_l, rho_v) -> (log theta, rho_l, log rho_v)."""
     y = np.asarray(y, dtype=np.float64)
@@ -70,9 +76,9 @@ def from_net_outputs(o):
 
 def normalisation(x, y):
     """Means and scales (population standard deviation; 1 where it is no more than 1e-9 of
-    the mean's magnitude, i.e. a constant column up to rounding) of the inputs and of the
-    transformed targets, returned as (in_mean, in_scale, out_mean, out_scale)."""
-    x = np.asarray(x, dtype=np.float64)
+    the mean's magnitude, i.e. a constant column up to rounding) of the input features and
+    of the transformed targets, returned as (in_mean, in_scale, out_mean, out_scale)."""
+    x = features(x)
     t = to_net_targets(y)
 
     def ms(a):
@@ -87,7 +93,7 @@ def forward(theta, x, norm, bf16=True):
     """Returns (predictions (theta, rho_l, rho_v), standardised outputs, cache)."""
     W1, b1, W2, b2, W3, b3 = unpack(bf16_round(theta) if bf16 else theta)
     in_m, in_s, out_m, out_s = (np.asarray(v, dtype=np.float64) for v in norm)
-    xn = (np.asarray(x, dtype=np.float64) - in_m) / in_s
+    xn = (features(x) - in_m) / in_s
     z1 = xn @ W1.T + b1
     a1 = gelu(z1)
     z2 = a1 @ W2.T + b2
@@ -131,11 +137,15 @@ def adam_step(theta, m, v, g, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def invert_kappa(theta, norm, t_over_tc, tau, target, lo=0.0, hi=0.95, iters=40):
     """Bisection for kappa with predicted theta(T, kappa, tau) = target (theta decreases
-    with kappa)."""
+    with kappa, Eq. 22); NaN when the target is outside [theta(hi), theta(lo)]."""
+    def th(k):
+        return forward(theta, np.array([[t_over_tc, k, tau]]), norm)[0][0, 0]
+
+    if not (th(lo) >= target >= th(hi)):
+        return float("nan")
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        y, _, _ = forward(theta, np.array([[t_over_tc, mid, tau]]), norm)
-        if y[0, 0] > target:
+        if th(mid) > target:
             lo = mid
         else:
             hi = mid

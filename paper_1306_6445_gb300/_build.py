@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblb_gb300.so")
-SOURCES = ["lb_api.cu", "lb_kernels.cu", "lb_thermo.cpp", "lb_noalloc.cu", "lb_batch.cu"]
+SOURCES = ["lb_api.cu", "lb_kernels.cu", "lb_thermo.cpp", "lb_noalloc.cu", "lb_batch.cu",
+           "lb_mlp.cu"]
 HEADERS = ["lb_internal.h", "lb_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
@@ -37,7 +38,7 @@ def nvcc() -> str:
 
 def _deps():
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
-    deps.append(os.path.join(ROOT, "include", "lb.h"))
+    deps += [os.path.join(ROOT, "include", h) for h in ("lb.h", "lb_mlp.h")]
     return deps
 
 

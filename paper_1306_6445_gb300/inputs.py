@@ -100,3 +100,28 @@ def batch_draws(n: int = 512, seed: int = DEFAULT_SEED):
             "tau_v": float(rng.uniform(0.6, 1.2)),
         })
     return out
+
+
+def mlp_init(seed: int = DEFAULT_SEED, n_in: int = 3, hidden: int = 64, n_out: int = 3):
+    """Initial parameters of the surrogate network as one float32 vector in the layout
+    W1[h][in], b1[h], W2[h][h], b2[h], W3[out][h], b3[out]: weights uniform in
+    +-sqrt(6 / (fan_in + fan_out)) (Glorot & Bengio 2010), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+        a = np.sqrt(6.0 / (fi + fo))
+        parts += [rng.uniform(-a, a, fo * fi), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_random_data(n: int, seed: int = DEFAULT_SEED):
+    """Random training pairs for gradient checks: x = (T/T_c, kappa, tau_v) uniform over the
+    sweep's ranges, y = (sigma, rho_l, rho_v) positive and spread over the ranges the
+    sweep produces (sigma and rho_v log-uniform). float32, n x 3 each."""
+    rng = np.random.default_rng(seed)
+    x = np.stack([rng.uniform(0.65, 0.95, n), rng.uniform(0.0, 0.95, n),
+                  rng.uniform(0.6, 1.2, n)], axis=1)
+    y = np.stack([np.exp(rng.uniform(np.log(2e-5), np.log(1e-2), n)),
+                  rng.uniform(0.3, 0.6, n), np.exp(rng.uniform(np.log(1e-3), np.log(0.15), n))],
+                 axis=1)
+    return x.astype(np.float32), y.astype(np.float32)

@@ -35,7 +35,13 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
             "lb_batch_steps_done", "lb_batch_size", "lb_batch_last_error", "lb_batch_free",
-            "lb_strip_widths"]
+            "lb_strip_widths",
+            # include/lb_mlp.h
+            "lb_mlp_create", "lb_mlp_set_params", "lb_mlp_get_params", "lb_mlp_set_data",
+            "lb_mlp_get_norm", "lb_mlp_set_norm", "lb_mlp_loss_grad", "lb_mlp_train",
+            "lb_mlp_steps_done", "lb_mlp_forward", "lb_mlp_invert_kappa", "lb_mlp_last_error",
+            "lb_mlp_free"]
+MLP_PARAMS = 4611
 
 
 class LBError(RuntimeError):
@@ -61,6 +67,11 @@ class c_lb_lattice_desc(C.Structure):
                 ("kappa", C.c_double), ("sigma_force", C.c_double), ("rates", c_lb_rates)]
 
 
+class c_lb_mlp_norm(C.Structure):
+    _fields_ = [("in_mean", C.c_float * 3), ("in_scale", C.c_float * 3),
+                ("out_mean", C.c_float * 3), ("out_scale", C.c_float * 3)]
+
+
 _lib = None
 
 
@@ -75,6 +86,7 @@ def load_library():
     lib = C.CDLL(LIB_PATH)
     P, I, D, SZ = C.c_void_p, C.c_int, C.c_double, C.c_size_t
     DP = C.POINTER(C.c_double)
+    F, FP = C.c_float, C.POINTER(C.c_float)
     sig = {
         "lb_pitch": (SZ, [I, I]),
         "lb_buffer_bytes": (SZ, [I, I, I]),
@@ -118,6 +130,19 @@ def load_library():
         "lb_batch_last_error": (C.c_char_p, [P]),
         "lb_batch_free": (None, [P]),
         "lb_strip_widths": (I, [I, I, C.POINTER(I), I]),
+        "lb_mlp_create": (I, [C.POINTER(P), I, P]),
+        "lb_mlp_set_params": (I, [P, FP]),
+        "lb_mlp_get_params": (I, [P, FP]),
+        "lb_mlp_set_data": (I, [P, FP, FP, I]),
+        "lb_mlp_get_norm": (I, [P, C.POINTER(c_lb_mlp_norm)]),
+        "lb_mlp_set_norm": (I, [P, C.POINTER(c_lb_mlp_norm)]),
+        "lb_mlp_loss_grad": (I, [P, FP, FP]),
+        "lb_mlp_train": (I, [P, I, F, F, F, F, FP]),
+        "lb_mlp_steps_done": (C.c_longlong, [P]),
+        "lb_mlp_forward": (I, [P, FP, FP, I]),
+        "lb_mlp_invert_kappa": (I, [P, FP, I, F, F, FP]),
+        "lb_mlp_last_error": (C.c_char_p, [P]),
+        "lb_mlp_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -538,6 +563,116 @@ class Batch:
         if getattr(self, "b", None):
             load_library().lb_batch_free(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------
+# surrogate network (include/lb_mlp.h)
+# ------------------------------------------------------------------------------------
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _f32(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a if shape is None else a.reshape(shape)
+
+
+class MLP:
+    """The 3-64-64-3 surrogate (T/T_c, kappa, tau_v) -> (sigma, rho_l, rho_v), trained and
+    evaluated by the library's kernels (lb_mlp_*), on torch's current stream."""
+
+    def __init__(self, max_samples: int = 4096, stream=None):
+        lib = load_library()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.m = C.c_void_p()
+        self._check(lib.lb_mlp_create(C.byref(self.m), int(max_samples), stream),
+                    "lb_mlp_create")
+
+    def _check(self, status, where):
+        if status != LB_OK:
+            msg = ""
+            if getattr(self, "m", None):
+                raw = load_library().lb_mlp_last_error(self.m)
+                msg = raw.decode() if raw else ""
+            raise LBError(status, where, msg)
+
+    def set_params(self, params):
+        p = _f32(params)
+        if p.size != MLP_PARAMS:
+            raise LBError(LB_EINVAL, "lb_mlp_set_params", f"need {MLP_PARAMS} values")
+        self._check(load_library().lb_mlp_set_params(self.m, _fp(p)), "lb_mlp_set_params")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(load_library().lb_mlp_get_params(self.m, _fp(out)), "lb_mlp_get_params")
+        return out
+
+    def set_data(self, x, y):
+        x, y = _f32(x), _f32(y)
+        if x.ndim != 2 or x.shape[1] != 3 or y.shape != x.shape:
+            raise LBError(LB_EINVAL, "lb_mlp_set_data", "x and y must be n x 3")
+        self._check(load_library().lb_mlp_set_data(self.m, _fp(x), _fp(y), x.shape[0]),
+                    "lb_mlp_set_data")
+
+    def norm(self):
+        nm = c_lb_mlp_norm()
+        self._check(load_library().lb_mlp_get_norm(self.m, C.byref(nm)), "lb_mlp_get_norm")
+        return tuple(np.array(list(getattr(nm, f)), dtype=np.float32)
+                     for f in ("in_mean", "in_scale", "out_mean", "out_scale"))
+
+    def set_norm(self, norm):
+        nm = c_lb_mlp_norm()
+        for f, v in zip(("in_mean", "in_scale", "out_mean", "out_scale"), norm):
+            getattr(nm, f)[:] = [float(t) for t in v]
+        self._check(load_library().lb_mlp_set_norm(self.m, C.byref(nm)), "lb_mlp_set_norm")
+
+    def loss_grad(self):
+        loss = C.c_float()
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(load_library().lb_mlp_loss_grad(self.m, C.byref(loss), _fp(g)),
+                    "lb_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, steps: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8) -> float:
+        loss = C.c_float()
+        self._check(load_library().lb_mlp_train(self.m, int(steps), lr, beta1, beta2, eps,
+                                                C.byref(loss)), "lb_mlp_train")
+        return loss.value
+
+    @property
+    def steps_done(self) -> int:
+        return int(load_library().lb_mlp_steps_done(self.m))
+
+    def forward(self, x) -> np.ndarray:
+        x = _f32(x)
+        n = x.shape[0]
+        y = np.empty((n, 3), dtype=np.float32)
+        self._check(load_library().lb_mlp_forward(self.m, _fp(x), _fp(y), n), "lb_mlp_forward")
+        return y
+
+    def invert_kappa(self, queries, kappa_lo: float = 0.0, kappa_hi: float = 0.95) -> np.ndarray:
+        """queries: n x 3 of (T/T_c, tau_v, sigma_target); NaN where not bracketed."""
+        q = _f32(queries)
+        n = q.shape[0]
+        out = np.empty(n, dtype=np.float32)
+        self._check(load_library().lb_mlp_invert_kappa(self.m, _fp(q), n, kappa_lo, kappa_hi,
+                                                       _fp(out)), "lb_mlp_invert_kappa")
+        return out
+
+    def close(self):
+        if getattr(self, "m", None):
+            load_library().lb_mlp_free(self.m)
+            self.m = None
 
     def __del__(self):
         try:

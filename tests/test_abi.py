@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every function include/lb.h declares; host-only
+"""The C-ABI library loads and exports every function include/*.h declares; host-only
 helpers (no GPU work) agree with the oracle's thermodynamics. CPU only."""
 import ctypes
 import os
@@ -23,14 +23,19 @@ def lbm():
 
 
 def header_functions():
-    text = open(os.path.join(ROOT, "include", "lb.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^[\w \*]*?\b(lb_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^[\w \*]*?\b(lb_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_documented_entry_points():
     names = header_functions()
-    for need in ("lb_init", "lb_step", "lb_get_rho", "lb_get_u", "lb_reduce", "lb_free"):
+    for need in ("lb_init", "lb_step", "lb_get_rho", "lb_get_u", "lb_reduce", "lb_free",
+                 "lb_mlp_train", "lb_mlp_forward", "lb_mlp_loss_grad", "lb_mlp_invert_kappa"):
         assert need in names
 
 

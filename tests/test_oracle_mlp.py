@@ -76,7 +76,9 @@ def test_gradient_matches_torch_autograd():
     th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
     sizes = [int(np.prod(s)) for s in M.SIZES]
     W1, b1, W2, b2, W3, b3 = (p.reshape(s) for p, s in zip(th.split(sizes), M.SIZES))
-    xn = (torch.tensor(x) - in_m) / in_s
+    xt = torch.tensor(x)
+    xn = (torch.stack([torch.log(1 - xt[:, 0]), torch.log(1 - xt[:, 1]), xt[:, 2]], dim=1)
+          - in_m) / in_s
     a1 = torch.nn.functional.gelu(xn @ W1.T + b1)
     a2 = torch.nn.functional.gelu(a1 @ W2.T + b2)
     o = a2 @ W3.T + b3
@@ -115,7 +117,7 @@ def test_forward_closed_form_with_zero_hidden_weights():
 def test_normalisation_standardises_the_data():
     theta, x, y, norm = random_problem(n=50, seed=6)
     in_m, in_s, out_m, out_s = norm
-    xn = (x - in_m) / in_s
+    xn = (M.features(x) - in_m) / in_s
     assert np.allclose(xn.mean(0), 0, atol=1e-13) and np.allclose(xn.std(0), 1)
     t = (M.to_net_targets(y) - out_m) / out_s
     assert np.allclose(t.mean(0), 0, atol=1e-13) and np.allclose(t.std(0), 1)
@@ -143,20 +145,32 @@ def test_adam_matches_torch_optimizer():
 
 def test_inversion_finds_the_crossing_a_scan_brackets():
     theta, x, y, norm = random_problem(n=64, seed=8, scale=0.1)
-    # make theta strictly decreasing in kappa: only the kappa input reaches log theta
+    # make theta strictly decreasing in kappa: only the ln(1 - kappa) feature reaches the
+    # hidden layers, with positive weights, through units kept on GELU's increasing branch
+    # (z > 0 there) and positive output weights
     W1, b1, W2, b2, W3, b3 = M.unpack(theta)
     W1[:, 0] = 0.0
     W1[:, 2] = 0.0
-    W1[:, 1] = -np.abs(W1[:, 1]) - 0.05
-    b1[:] = 0.0
+    W1[:, 1] = np.abs(W1[:, 1]) * 0.1 + 0.01
+    b1[:] = 1.0
     W2 = np.abs(W2)
+    b2[:] = 0.0
     W3[0] = np.abs(W3[0]) + 0.01
     t = M.pack([W1, b1, W2, b2, W3, b3])
     ks = np.linspace(0, 0.95, 951)
     q = np.stack([np.full_like(ks, 0.8), ks, np.full_like(ks, 0.9)], axis=1)
     th = M.forward(t, q, norm)[0][:, 0]
     assert np.all(np.diff(th) < 0)
+    assert np.isnan(M.invert_kappa(t, norm, 0.8, 0.9, th[0] * 1.01))
+    assert np.isnan(M.invert_kappa(t, norm, 0.8, 0.9, th[-1] * 0.99))
     for target in (th[100] * 0.999, th[500], th[900] * 1.001):
         k = M.invert_kappa(t, norm, 0.8, 0.9, target)
         i = np.searchsorted(-th, -target)          # first grid point with theta <= target
         assert ks[i - 1] <= k <= ks[i] + 1e-9
+
+
+def test_features_closed_form():
+    x = np.array([[0.0, 0.0, 0.7], [0.5, 0.75, 1.1], [1 - np.exp(-3), 1 - np.exp(-2), 0.6]])
+    f = M.features(x)
+    assert np.allclose(f, [[0, 0, 0.7], [np.log(0.5), np.log(0.25), 1.1], [-3, -2, 0.6]],
+                       atol=1e-15)
