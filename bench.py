@@ -12,7 +12,10 @@ resident); `e2e` = the same through the C ABI with host buffers (populations in 
 pinned host memory, density field out to pinned host memory, every step);
 `roofline` = the fused kernel's algorithmic bytes per launch / its live CUDA-event
 duration against the measured HBM copy bandwidth; `fp64` = the same workload in FP64;
-`cpu_baseline` = the FP64 numpy oracle on one host core over a bounded sample.
+`cpu_baseline` = the FP64 numpy oracle on one host core over a bounded sample;
+`batched` = the 512-droplet sweep in one persistent launch per step; `surrogate` = the
+network trained on a converged batched sweep and the kappa it picks, judged by Laplace
+runs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -59,6 +62,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=10000,
                     help="time steps of the 512-lattice batched sweep (0: skip it)")
     ap.add_argument("--batch-lattices", type=int, default=512)
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate leg (converged sweep, training, judged kappa)")
     return ap.parse_args()
 
 
@@ -298,6 +303,50 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
     }
 
 
+def surrogate_leg(lbm, torch, n_train=512):
+    """The surrogate end to end: a converged batched Laplace sweep of n_train droplets
+    (128^2, R = 32, 24000 steps, reading averaged over the last 2048), full-batch Adam
+    training in the library's kernels, then kappa for the hardest targets (the smallest
+    sigma per temperature, kappa near 0.93) judged by a plain Laplace run, against the
+    Eq. 22 law calibrated by a kappa = 0 run."""
+    import numpy as np
+    from paper_1306_6445_gb300 import surrogate, sweep
+
+    X = sweep.training_points(n_train)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Y = sweep.laplace_points(lbm, X)
+    t_sweep = time.perf_counter() - t0
+    ok = Y[:, 3] == 0
+    t0 = time.perf_counter()
+    net, losses = surrogate.fit(lbm, X[ok], Y[ok, :3])
+    t_fit = time.perf_counter() - t0
+    adam_steps = sum(s for s, _ in surrogate.SCHEDULE)
+    # per-step time of the training kernels alone (graph replays, no host work between)
+    t0 = time.perf_counter()
+    net.train(1000, 1e-5)
+    us_step = (time.perf_counter() - t0) / 1000 * 1e6
+    g = np.array([(0.7, 0.7, 5e-4), (0.7, 1.1, 5e-4), (0.8, 0.7, 2.5e-4), (0.8, 1.1, 2.5e-4),
+                  (0.9, 0.7, 9e-5), (0.9, 1.1, 9e-5)])
+    res = surrogate.tune_kappa(lbm, net, g[:, 0], g[:, 1], g[:, 2], tol=0.02, max_rounds=0)
+    s0 = surrogate.sweep_points(lbm, g[:, 0], np.zeros(len(g)), g[:, 1])
+    s_law = surrogate.sweep_points(lbm, g[:, 0], 1 - g[:, 2] / s0, g[:, 1])
+    net.close()
+    e_net, e_law = np.abs(res["rel_err"]), np.abs(s_law / g[:, 2] - 1)
+    return {
+        "train_samples": int(ok.sum()), "sweep_seconds": round(t_sweep, 3),
+        "sweep_droplets_per_s": round(n_train / t_sweep, 1),
+        "fit_seconds": round(t_fit, 3), "adam_steps": adam_steps,
+        "us_per_adam_step": round(us_step, 2),
+        "train_samples_per_s": round(int(ok.sum()) / (us_step * 1e-6), 0),
+        "final_loss": losses[-1],
+        "judged_targets": len(g), "laplace_runs_per_target": float(res["runs"].mean()),
+        "sigma_err_net_max": round(float(e_net.max()), 5),
+        "sigma_err_law_max": round(float(e_law.max()), 5),
+        "law_calibration_runs_per_target": 1,
+    }
+
+
 def cpu_baseline(nx, ny, budget_s=20.0):
     """The FP64 numpy oracle, single thread, on the same droplet lattice: as many whole
     steps as fit in ~budget_s (at least one). Runs in a child process so the BLAS thread
@@ -392,6 +441,7 @@ def native(args):
     batched = None
     if args.batch_steps > 0:
         batched = batched_sweep(lbm, torch, inputs, args.batch_lattices, args.batch_steps)
+    surr = None if args.no_surrogate else surrogate_leg(lbm, torch)
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(nx, ny)
         line = {
@@ -404,6 +454,7 @@ def native(args):
                        "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"},
             "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "batched": batched,
+            "surrogate": surr,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
