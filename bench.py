@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--variant", type=int, default=-1, help="step-kernel variant (-1: library default)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="step-kernel variant (-1: chosen by the library's autotuner)")
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
     ap.add_argument("--batch-steps", type=int, default=10000,
                     help="time steps of the 512-lattice batched sweep (0: skip it)")
@@ -163,9 +164,11 @@ def droplet_setup(lbm, inputs, nx, ny):
 def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist, launch=None):
     eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
     lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec)
+    lat.set_rho_u(rho)
     if launch is not None and launch[0] >= 0:
         lbm.lb_set_launch(lat.ctx, launch[0], launch[1])
-    lat.set_rho_u(rho)
+    else:
+        lat.autotune(5)          # the library's own launch autotuner (state unchanged)
     shape = lbm.lb_get_launch(lat.ctx)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):

@@ -108,13 +108,23 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
                      double sigma_force, const lb_rates *rates, int prec, int bc, void *stream,
                      void *f_a, void *f_b);
 
-/* Number of compiled variants of the step kernel (strip width x shared-memory ring depth). */
+/* Number of compiled variants of the step kernel (strip width x shared-memory ring depth
+ * x row groups sharing one ring). */
 int lb_launch_variants(void);
 
 /* Choose the step kernel's variant (0 .. lb_launch_variants()-1) and the number of rows
- * each CTA marches over (rows = 0: size the grid to one full wave of resident CTAs).
+ * each CTA marches over (rows = 0: about three waves of resident CTAs, at least 8 rows).
  * Synchronises the stream. Errors: LB_EINVAL for an unknown variant or rows < 0. */
 lb_status lb_set_launch(lb_ctx *ctx, int variant, int rows);
+
+/* Autotuner: time every compiled variant with rows per CTA from {default, 6, 8, 9, 10,
+ * 11, 12, 14, 16, 20, 24} (at most ny) on this lattice and keep the fastest. Each
+ * candidate runs one untimed and `trial_steps` >= 1 timed launches of the step kernel
+ * that read the current state and write the spare buffer, so the state and the step
+ * count are unchanged. Per-site results do not depend on the choice. Writes the choice
+ * if the pointers are not NULL. Synchronises. Errors: LB_EINVAL, LB_ECUDA, and the
+ * sticky errors of lb_sync. */
+lb_status lb_autotune(lb_ctx *ctx, int trial_steps, int *variant, int *rows);
 
 /* Current launch: variant, lattice columns per CTA, rows per CTA, resident CTAs per SM. */
 lb_status lb_get_launch(const lb_ctx *ctx, int *variant, int *tx, int *rows, int *ctas_per_sm);

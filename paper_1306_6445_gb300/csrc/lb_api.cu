@@ -345,6 +345,61 @@ lb_status lb_set_launch(lb_ctx *c, int variant, int rows) {
     return apply_launch(c, variant, rows);
 }
 
+lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (trial_steps < 1) return fail(c, LB_EINVAL, "lb_autotune: trial_steps < 1");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    static const int cand[] = {0, 6, 8, 9, 10, 11, 12, 14, 16, 20, 24};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LB_CUDA(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, LB_ECUDA, "lb_autotune: cudaEventCreate failed");
+    }
+    float best_ms = 0.f;
+    int best_v = c->launch.variant, best_r = c->launch.rows;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < lbm::step_variant_count() && e == cudaSuccess; ++v) {
+        int tried_rows[16], n_tried = 0;
+        for (int r : cand) {
+            if ((s = apply_launch(c, v, r)) != LB_OK) break;
+            const int rr = c->launch.rows;
+            bool seen = false;
+            for (int i = 0; i < n_tried; ++i) seen |= tried_rows[i] == rr;
+            if (seen) continue;
+            tried_rows[n_tried++] = rr;
+            auto once = [&]() {
+                return lbm::launch_step(c->prec, c->consts, c->geom, c->launch, &c->tmap[c->cur],
+                                        c->f[c->cur ^ 1], c->d_err, c->stream);
+            };
+            e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+                best_r = rr;
+            }
+        }
+        if (s != LB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != LB_OK) return s;
+    if (e != cudaSuccess)
+        return fail(c, LB_ECUDA, std::string("lb_autotune: ") + cudaGetErrorString(e));
+    if ((s = apply_launch(c, best_v, best_r)) != LB_OK) return s;
+    if (variant) *variant = best_v;
+    if (rows) *rows = best_r;
+    return sync_and_check(c);
+}
+
 lb_status lb_debug_stall_row(lb_ctx *c, int row) {
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;

@@ -24,6 +24,9 @@ struct DevConsts {
     T two_over_G;
     T G, kG2, sig_coef;
     T s_e, s_z, s_q, s_v;
+    // Eq. 17 coefficients per relaxed moment k: (1 - s_k), s_k, (1 - s_k/2) and the source
+    // weights 3 s_k / 2 (e, zeta) and -s_v (p_xx, p_xy), rounded once from FP64
+    T e_keep, e_half, e_src, z_keep, z_half, z_src, q_keep, q_half, v_keep, v_half, v_src;
     int stall_row;
 };
 
@@ -46,6 +49,10 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.two_over_G = T(c.two_over_G);
     d.G = T(c.G); d.kG2 = T(c.kG2); d.sig_coef = T(c.sig_coef);
     d.s_e = T(c.s_e); d.s_z = T(c.s_z); d.s_q = T(c.s_q); d.s_v = T(c.s_v);
+    d.e_keep = T(1.0 - c.s_e); d.e_half = T(1.0 - 0.5 * c.s_e); d.e_src = T(1.5 * c.s_e);
+    d.z_keep = T(1.0 - c.s_z); d.z_half = T(1.0 - 0.5 * c.s_z); d.z_src = T(1.5 * c.s_z);
+    d.q_keep = T(1.0 - c.s_q); d.q_half = T(1.0 - 0.5 * c.s_q);
+    d.v_keep = T(1.0 - c.s_v); d.v_half = T(1.0 - 0.5 * c.s_v); d.v_src = T(-c.s_v);
     d.stall_row = c.stall_row;
     return d;
 }
@@ -243,20 +250,19 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V tr = Qxx + Qyy;
 
     // Eq. 17, written as (1 - s) m + s m_eq + (1 - s/2) S + C
-    const T se = P.s_e, sz = P.s_z, sq = P.s_q, sv = P.s_v;
     const V ms0 = rho;
-    const V ms1 = vfma(V::all(T(1) - se), m1, vfma(V::all(se), meq1,
-                  vfma(V::all(T(1) - T(0.5) * se), S1, V::all(T(1.5) * se) * tr)));
-    const V ms2 = vfma(V::all(T(1) - sz), m2, vfma(V::all(sz), meq2,
-                  V::all(T(0)) - vfma(V::all(T(1) - T(0.5) * sz), S1, V::all(T(1.5) * sz) * tr)));
+    const V ms1 = vfma(V::all(P.e_keep), m1, vfma(V::all(P.s_e), meq1,
+                  vfma(V::all(P.e_half), S1, V::all(P.e_src) * tr)));
+    const V ms2 = vfma(V::all(P.z_keep), m2, vfma(V::all(P.s_z), meq2,
+                  V::all(T(0)) - vfma(V::all(P.z_half), S1, V::all(P.z_src) * tr)));
     const V ms3 = jx + Fx;
-    const V ms4 = vfma(V::all(T(1) - sq), m4, V::all(T(0)) - vfma(V::all(sq), rvx, V::all(T(1) - T(0.5) * sq) * Fx));
+    const V ms4 = vfma(V::all(P.q_keep), m4, V::all(T(0)) - vfma(V::all(P.s_q), rvx, V::all(P.q_half) * Fx));
     const V ms5 = jy + Fy;
-    const V ms6 = vfma(V::all(T(1) - sq), m6, V::all(T(0)) - vfma(V::all(sq), rvy, V::all(T(1) - T(0.5) * sq) * Fy));
-    const V ms7 = vfma(V::all(T(1) - sv), m7, vfma(V::all(sv), meq7,
-                  vfma(V::all(T(1) - T(0.5) * sv), S7, V::all(-sv) * (Qxx - Qyy))));
-    const V ms8 = vfma(V::all(T(1) - sv), m8, vfma(V::all(sv), meq8,
-                  vfma(V::all(T(1) - T(0.5) * sv), S8, V::all(-sv) * Qxy)));
+    const V ms6 = vfma(V::all(P.q_keep), m6, V::all(T(0)) - vfma(V::all(P.s_q), rvy, V::all(P.q_half) * Fy));
+    const V ms7 = vfma(V::all(P.v_keep), m7, vfma(V::all(P.s_v), meq7,
+                  vfma(V::all(P.v_half), S7, V::all(P.v_src) * (Qxx - Qyy))));
+    const V ms8 = vfma(V::all(P.v_keep), m8, vfma(V::all(P.s_v), meq8,
+                  vfma(V::all(P.v_half), S8, V::all(P.v_src) * Qxy)));
 
     // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
     const V c9 = V::all(T(1.0 / 9.0)), c18 = V::all(T(1.0 / 18.0)), c36 = V::all(T(1.0 / 36.0));

@@ -5,7 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/lb.h"
+#include "lb.h"
 
 namespace lbm {
 

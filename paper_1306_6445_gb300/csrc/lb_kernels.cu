@@ -78,15 +78,20 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase with the given parity; give up after ~1 s (returns false).
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+// Slow path of mbar_wait_bounded: poll until the phase completes or ~1 s has passed.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity) {
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (global_ns() - t0 > 1000000000ull) return false;
     }
+}
+
+// Wait for the phase with the given parity; give up after ~1 s (returns false). The first
+// try is inline: in the steady state the row has landed and no call is made.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
@@ -148,16 +153,20 @@ __device__ __forceinline__ V2<T> rho_pair(const V2<T> (&f)[9]) {
     return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
 }
 
+// rows of the psi ring for G row groups: at least 3G + 1 (see march), a power of two
+template <int G>
+__host__ __device__ constexpr int psi_ring_rows() { return G == 1 ? 4 : 8; }
+
 // shared-memory layout of k_pull_collide: S ring stages (each rounded up to 128 bytes),
-// the four-row psi ring, then S mbarriers
-template <typename T, int TX, int S>
+// the psi ring, then S mbarriers
+template <typename T, int TX, int S, int G>
 __host__ __device__ constexpr size_t step_bar_offset() {
     return (size_t)S * (((9u * (TX + 8) * sizeof(T)) + 127u) / 128u * 128u) +
-           (((size_t)4 * (TX + 4) * sizeof(T) + 15u) / 16u * 16u);
+           (((size_t)psi_ring_rows<G>() * (TX + 4) * sizeof(T) + 15u) / 16u * 16u);
 }
-template <typename T, int TX, int S>
+template <typename T, int TX, int S, int G>
 __host__ __device__ constexpr size_t step_smem_bytes() {
-    return step_bar_offset<T, TX, S>() + (size_t)S * 8 + 128;   // + room to align the base
+    return step_bar_offset<T, TX, S, G>() + (size_t)S * 8 + 128;   // + room to align the base
 }
 
 template <typename T>
@@ -230,42 +239,55 @@ __device__ __forceinline__ void grid_dependents_launch() {
 }
 
 // One time step for one strip of a lattice: columns x0 .. x0+w-1 (w <= TX, x0 a multiple of
-// 4) and rows yb .. yb+n-1, visited in order k = 0 .. n-1, y_k = start + k*dir. In the
-// single-lattice kernel dir = +1 for even blockIdx.y and -1 for odd, so that neighbouring
-// row blocks reach their shared apron rows at the same time and the second read hits L2.
-// Lattice row start + (j-2)*dir is the j-th row requested into the ring (slot j mod S);
-// iteration k reads ring rows j = k+2..k+4 to form psi(y_k + dir), then collides row y_k
-// with psi(y_k - 1 .. y_k + 1). After the barrier of iteration k, ring row k+2 is dead and
-// its slot receives row k+2+S, i.e. S-2 iterations ahead of use.
+// 4) and rows yb .. yb+n-1, visited from `start` in direction dir. In the single-lattice
+// kernel dir = +1 for even blockIdx.y and -1 for odd, so that neighbouring row blocks
+// reach their shared apron rows at the same time and the second read hits L2.
+//
+// The CTA holds G row groups of TX/2 threads. Iteration k collides the G rows
+// y_k + g dir (y_k = start + G k dir), group g taking row y_k + g dir, with psi of the rows
+// around it; before that, group g pulls row y_k + (G + g) dir (the row it collides next
+// iteration, kept in registers) and forms its psi. Lattice row start + (j-2) dir is the
+// j-th row requested into the ring (slot j mod S): iteration k reads ring rows
+// G k + G + 1 .. G k + 2G + 2; after its barrier rows up to G k + 2G are dead and their
+// slots receive rows up to G k + 2G + S, i.e. (S - 2) / G iterations ahead of use.
+// Psi of row Y sits in psi-ring row Y mod psi_ring_rows<G>(); a row is written one
+// iteration before the last collision that reads it, and the rows read and written in
+// two consecutive iterations span 3G + 1 rows. With walls, psi of rows -1 and ny is
+// that of rows 0 and ny-1 (the collision reads those rows instead).
 //
 // The caller has initialised the S ring mbarriers (fresh, phase 0) and waited for the
 // previous grid. Returns 0, or ERR_TIMEOUT after a bounded wait gave up (then every copy
 // still in flight has landed, or its own bounded wait gave up too).
-template <typename T, int EOS, bool WALLS, int TX, int S>
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
 __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ gout,
                                      const DevConsts<T> &P, const int nx, const int ny,
                                      const int pitch, const unsigned plane, const int x0,
                                      const int w, const int yb, const int n, const int dir,
                                      unsigned char *smem_raw, bool &bad) {
-    static_assert(S >= 5, "the prologue needs ring rows 0..4 in flight");
+    static_assert(G == 1 || G == 2, "one or two row groups");
+    static_assert(S >= G + 4, "ring rows of one iteration plus one row in flight");
     static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
-    constexpr int NT = TX / 2;
+    constexpr int NT = TX / 2;      // threads per row group
     constexpr int BW = TX + 8;      // ring row: columns x0-4 .. x0+TX+3 -> ring col = x - x0 + 4
     constexpr int RW = TX + 4;      // psi row: columns x0-2 .. x0+TX+1 -> psi col = x - x0 + 2
+    constexpr int PR = psi_ring_rows<G>();
     constexpr uint32_t STAGE_BYTES = 9u * BW * sizeof(T);
     constexpr int STAGE_ELEMS = (int)(((STAGE_BYTES + 127u) / 128u) * 128u / sizeof(T));
     T *ring = reinterpret_cast<T *>(smem_raw);                 // S stages, 128-byte aligned
-    T *psis = ring + S * STAGE_ELEMS;                           // [4][RW]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>());
+    T *psis = ring + S * STAGE_ELEMS;                           // [PR][RW]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>());
 
-    const int t = threadIdx.x;
+    const int grp = G == 1 ? 0 : (int)threadIdx.x / NT;      // row group
+    const int t = (int)threadIdx.x - grp * NT;                // thread within the group
+    const bool lead = threadIdx.x == 0;                       // requests the ring rows
     const int c0 = 2 * t;                 // first of the thread's two columns, relative to x0
     const bool act = c0 < w;
     const bool both = c0 + 1 < w;
     const int start = dir > 0 ? yb : yb + n - 1;
-    const int nj = n + 4;                 // ring rows j = 0 .. n+3
+    const int K = (n + G - 1) / G;        // iterations
+    const int nj = G * K + G + 3;         // ring rows j = 0 .. nj-1
 
-    // thread 0 requests ring rows in order
+    // the lead thread requests ring rows in order
     int ji = 0, si = 0;
     auto issue_upto = [&](int jmax) {
         for (; ji <= jmax && ji < nj; ++ji) {
@@ -281,29 +303,21 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
         }
     };
 
-    if (t == 0) issue_upto(S - 1);
+    if (lead) issue_upto(S - 1);
 
-    auto stage = [&](int s) -> const T * { return ring + s * STAGE_ELEMS; };
+    auto stage = [&](int j) -> const T * { return ring + (j % S) * STAGE_ELEMS; };
+    auto wait_row = [&](int j) -> bool {
+        return mbar_wait_bounded(&bar[j % S], (uint32_t)((j / S) & 1));
+    };
 
-    // psi of lattice row Y from ring slots (row Y - dir, Y, Y + dir) into psi slot Y & 3,
-    // keeping the pulled populations of the thread's two sites in `keep`. With walls, the
-    // rows -1 and ny take the psi of rows 0 and ny-1 (already in the psi ring).
-    auto psi_row = [&](int Y, int s_back, int s_mid, int s_fwd, V2<T> (&keep)[9]) {
-        T *ps = psis + (Y & 3) * RW;
-        if (WALLS && (Y < 0 || Y >= ny)) {
-            const T *src = psis + ((Y < 0 ? 0 : ny - 1) & 3) * RW;
-            if (act) {
-                ps[c0 + 2] = src[c0 + 2];
-                if (both) ps[c0 + 3] = src[c0 + 3];
-            }
-            if (t == NT - 1) {
-                ps[1] = src[1];
-                ps[w + 2] = src[w + 2];
-            }
-            return;
-        }
-        const Ring<T> r = dir > 0 ? Ring<T>{stage(s_back), stage(s_mid), stage(s_fwd)}
-                                  : Ring<T>{stage(s_fwd), stage(s_mid), stage(s_back)};
+    // psi of lattice row Y (ring rows j-1, j, j+1 hold lattice rows Y - dir, Y, Y + dir)
+    // into psi-ring row Y, keeping the pulled populations of the thread's two sites in
+    // `keep`. With walls, rows outside the lattice are skipped (see above).
+    auto psi_row = [&](int Y, int j, V2<T> (&keep)[9]) {
+        if (WALLS && (Y < 0 || Y >= ny)) return;
+        T *ps = psis + (Y & (PR - 1)) * RW;
+        const Ring<T> r = dir > 0 ? Ring<T>{stage(j - 1), stage(j), stage(j + 1)}
+                                  : Ring<T>{stage(j + 1), stage(j), stage(j - 1)};
         const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
         if (act) {
             pull2<T, WALLS, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top);
@@ -322,36 +336,48 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             ps[w + 2] = psi.hi();
         }
     };
+    // psi-ring row holding psi of lattice row Y (walls: rows -1 and ny read rows 0, ny-1)
+    auto psi_at = [&](int Y) -> const T * {
+        if (WALLS) Y = Y < 0 ? 0 : (Y >= ny ? ny - 1 : Y);
+        return psis + (Y & (PR - 1)) * RW;
+    };
 
-    auto inc = [&](int s) { return (s + 1 == S) ? 0 : s + 1; };
-
-    // prologue: ring rows 0..3 give psi(start) (rows 1..3) and psi(start - dir) (rows 0..2)
+    // prologue: psi of rows start - dir .. start + (G-1) dir from ring rows 0 .. G+2;
+    // group g keeps the populations of row start + g dir (its first collision row).
+    // Group 0 also forms psi(start - dir), after psi(start), in the same threads.
     bool tmo = false;
+    int jw = 0;                                  // first ring row not yet seen complete
 #pragma unroll 1
-    for (int j = 0; j <= 3; ++j) tmo |= !mbar_wait_bounded(&bar[j], 0u);
+    for (int j = 0; j <= G + 2; ++j) {
+        tmo |= !wait_row(j);
+        if (!tmo) jw = j + 1;
+    }
     V2<T> fA[9], fB[9];
     if (!tmo) {
-        psi_row(start, 1, 2, 3, fA);
-        psi_row(start - dir, 0, 1, 2, fB);
+        psi_row(start + grp * dir, grp + 2, fA);
+        if (grp == 0) psi_row(start - dir, 1, fB);
     }
-    int jw = 4;                                  // next ring row to wait for
-    int sa = 2 % S, sb = 3 % S, sc = 4 % S;      // slots of ring rows k+2, k+3, k+4
-    uint32_t phc = (uint32_t)((4 / S) & 1);      // phase parity of ring row k+4
+    // ring rows 0 .. G are dead now: refill their slots at once
+    tmo = __syncthreads_or(tmo);
+    if (!tmo && lead) issue_upto(S + G);
 
     auto body = [&](int k, V2<T> (&fc)[9], V2<T> (&fn)[9]) -> bool {
-        const int y = start + k * dir;
-        if (!tmo) {
-            tmo = !mbar_wait_bounded(&bar[sc], phc);
-            jw = k + 5;
+        const int y = start + G * k * dir;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int j = G * k + G + 3 + i;
+            if (!tmo) tmo = !wait_row(j);
+            if (!tmo) jw = j + 1;
         }
-        if (!tmo) psi_row(y + dir, sa, sb, sc, fn);
+        if (!tmo) psi_row(y + (G + grp) * dir, G * k + G + 2 + grp, fn);
         if (__syncthreads_or(tmo)) return false;
-        if (t == 0) issue_upto(k + 2 + S);     // ring row k+2 is dead: refill its slot
+        if (lead) issue_upto(G * k + 2 * G + S);   // refill the slots of the dead rows
 
-        if (act) {
-            const T *pm = psis + ((y - 1) & 3) * RW;
-            const T *p0 = psis + (y & 3) * RW;
-            const T *pp = psis + ((y + 1) & 3) * RW;
+        const int yr = y + grp * dir;            // this group's collision row
+        if (act && G * k + grp < n) {
+            const T *pm = psi_at(yr - 1);
+            const T *p0 = psi_at(yr);
+            const T *pp = psi_at(yr + 1);
             const int c = c0 + 2;
             const V2<T> m0 = lds_pair<T>(pm + c), z0 = lds_pair<T>(p0 + c), q0 = lds_pair<T>(pp + c);
             const T mL = pm[c - 1], mR = pm[c + 2], zL = p0[c - 1], zR = p0[c + 2];
@@ -369,12 +395,12 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             collide_pair<T>(fc, pn, P);
 
             const int x = x0 + c0;
-            const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH);
+            const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH);
 #pragma unroll
             for (int a = 0; a < 9; ++a) store_pair<T>(gout + (idx + a * plane), fc[a], both);
             // ghost images of columns 0, 1 (right of nx-1) and nx-2, nx-1 (left of 0)
             if (x < 2 || x + 1 >= nx - 2) {
-                const unsigned rowi = (unsigned)y * (unsigned)pitch;
+                const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const T v0 = fc[a].lo(), v1 = fc[a].hi();
@@ -386,30 +412,23 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                 }
             }
         }
-        sa = sb;
-        sb = sc;
-        sc = inc(sc);
-        if (sc == 0) phc ^= 1u;
         return true;
     };
 
     int k = 0;
-    bool ok = !tmo;
+    bool ok = !tmo;                              // the same in every thread (barrier above)
     if (ok) {
-        for (; k + 1 < n; k += 2) {
+        for (; k + 1 < K; k += 2) {
             if (!body(k, fA, fB) || !body(k + 1, fB, fA)) { ok = false; break; }
         }
-        if (ok && k < n) ok = body(k, fA, fB);
-    } else {
-        ok = !__syncthreads_or(true);
+        if (ok && k < K) ok = body(k, fA, fB);
     }
     if (!ok) {
-        // a bounded wait gave up: let the copies in flight land (each wait bounded), leave
-        if (t == 0) {
-            int s = jw % S;
-            for (int j = jw; j < ji; ++j, s = inc(s))
-                (void)mbar_wait_bounded(&bar[s], (uint32_t)((j / S) & 1));
-        }
+        // a bounded wait gave up: let every requested copy land (each wait bounded; the
+        // test hook's row was never requested), then leave
+        if (lead)
+            for (int j = jw; j < ji; ++j)
+                if (start + (j - 2) * dir != P.stall_row) (void)wait_row(j);
         __syncthreads();
         return ERR_TIMEOUT;
     }
@@ -433,15 +452,15 @@ __device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
 }
 
 // Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
-template <typename T, int EOS, bool WALLS, int TX, int S>
-__global__ void __launch_bounds__(TX / 2)
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+__global__ void __launch_bounds__(G * TX / 2)
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<T> P, const int nx, const int ny, const int pitch,
                const unsigned plane, const int rows, int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char *smem_raw = align_smem128(smem_dyn);
     if (threadIdx.x == 0) prefetch_tensormap(&tin);
-    init_ring_barriers<S>(reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>()),
+    init_ring_barriers<S>(reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>()),
                           false);
     // everything below reads the previous step's output or writes this step's: wait for
     // the previous grid to complete (programmatic dependent launch), then let the next one
@@ -451,7 +470,7 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     const int x0 = blockIdx.x * TX;
     const int yb = blockIdx.y * rows;
     bool bad = false;
-    const int st = march<T, EOS, WALLS, TX, S>(&tin, gout, P, nx, ny, pitch, plane, x0,
+    const int st = march<T, EOS, WALLS, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
                                                min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                (blockIdx.y & 1) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
@@ -462,14 +481,14 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
 // items (lattice, strip, row block), item i going to CTA i mod gridDim.x. Per-lattice
 // constants, buffers and TMA descriptors come from device tables; `phase` says which of a
 // lattice's two buffers holds the current state. Errors are recorded per lattice.
-template <typename T, int EOS, int TX, int S>
-__global__ void __launch_bounds__(TX / 2)
+template <typename T, int EOS, int TX, int S, int G>
+__global__ void __launch_bounds__(G * TX / 2)
 k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
              const BatchItem *__restrict__ items, const int n_items, const int phase,
              int *__restrict__ errs) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char *smem_raw = align_smem128(smem_dyn);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S>());
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>());
     init_ring_barriers<S>(bar, false);
     grid_dependency_wait();
     grid_dependents_launch();
@@ -480,7 +499,7 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
         const CUtensorMap *map = maps + 2 * it.lat + phase;
         if (threadIdx.x == 0) prefetch_tensormap(map);
         bool bad = false;
-        const int st = march<T, EOS, false, TX, S>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
+        const int st = march<T, EOS, false, TX, S, G>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
                                                    L.plane, it.x0, it.w, it.yb, it.n, it.dir,
                                                    smem_raw, bad);
         if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
@@ -720,17 +739,17 @@ k_reduce_final(const double *__restrict__ partials, int nblocks, double *__restr
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 
-template <typename T, int EOS, bool WALLS, int TX, int S>
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
 cudaError_t step_variant(const Consts &c, const Geom &g, int rows, const CUtensorMap &tin,
                          void *out, int *err, cudaStream_t st, bool configure) {
-    auto kern = k_pull_collide<T, EOS, WALLS, TX, S>;
-    constexpr size_t smem = step_smem_bytes<T, TX, S>();
+    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
     if (configure) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
-    cfg.blockDim = dim3(TX / 2);
+    cfg.blockDim = dim3(G * TX / 2);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     // programmatic dependent launch: this grid's CTAs may start their set-up while the
@@ -744,20 +763,20 @@ cudaError_t step_variant(const Consts &c, const Geom &g, int rows, const CUtenso
                               g.pitch, (unsigned)g.plane, rows, err);
 }
 
-template <typename T, int TX, int S>
+template <typename T, int TX, int S, int G>
 cudaError_t step_eos(const Consts &c, const Geom &g, int rows, const CUtensorMap &tin, void *out,
                      int *err, cudaStream_t st, bool configure) {
     const bool w = g.walls != 0;
     switch (c.eos_kind) {
         case LB_EOS_CS:
-            return w ? step_variant<T, LB_EOS_CS, true, TX, S>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_CS, false, TX, S>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_CS, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_CS, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
         case LB_EOS_EXP:
-            return w ? step_variant<T, LB_EOS_EXP, true, TX, S>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_EXP, false, TX, S>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_EXP, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_EXP, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
         default:
-            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
     }
 }
 
@@ -766,44 +785,49 @@ cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l,
                           const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                           bool configure) {
     switch (l.variant) {
-        case 0: return step_eos<T, 128, 5>(c, g, l.rows, tin, out, err, st, configure);
-        case 1: return step_eos<T, 128, 6>(c, g, l.rows, tin, out, err, st, configure);
-        case 2: return step_eos<T, 240, 5>(c, g, l.rows, tin, out, err, st, configure);
-        case 3: return step_eos<T, 64, 6>(c, g, l.rows, tin, out, err, st, configure);
+        case 0: return step_eos<T, 128, 5, 1>(c, g, l.rows, tin, out, err, st, configure);
+        case 1: return step_eos<T, 128, 6, 1>(c, g, l.rows, tin, out, err, st, configure);
+        case 2: return step_eos<T, 240, 5, 1>(c, g, l.rows, tin, out, err, st, configure);
+        case 3: return step_eos<T, 64, 6, 1>(c, g, l.rows, tin, out, err, st, configure);
+        case 4: return step_eos<T, 128, 6, 2>(c, g, l.rows, tin, out, err, st, configure);
+        case 5: return step_eos<T, 128, 8, 2>(c, g, l.rows, tin, out, err, st, configure);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int EOS, bool WALLS, int TX, int S>
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
 int occupancy_variant() {
     int n = 0;
-    constexpr size_t smem = step_smem_bytes<T, TX, S>();
-    auto kern = k_pull_collide<T, EOS, WALLS, TX, S>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX / 2, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, G * TX / 2, smem) != cudaSuccess)
+        return 0;
     return n;
 }
 
-template <typename T, int TX, int S>
+template <typename T, int TX, int S, int G>
 int occupancy_eos(int eos, bool w) {
     switch (eos) {
         case LB_EOS_CS:
-            return w ? occupancy_variant<T, LB_EOS_CS, true, TX, S>() : occupancy_variant<T, LB_EOS_CS, false, TX, S>();
+            return w ? occupancy_variant<T, LB_EOS_CS, true, TX, S, G>() : occupancy_variant<T, LB_EOS_CS, false, TX, S, G>();
         case LB_EOS_EXP:
-            return w ? occupancy_variant<T, LB_EOS_EXP, true, TX, S>() : occupancy_variant<T, LB_EOS_EXP, false, TX, S>();
+            return w ? occupancy_variant<T, LB_EOS_EXP, true, TX, S, G>() : occupancy_variant<T, LB_EOS_EXP, false, TX, S, G>();
         default:
-            return w ? occupancy_variant<T, LB_EOS_PIECEWISE, true, TX, S>() : occupancy_variant<T, LB_EOS_PIECEWISE, false, TX, S>();
+            return w ? occupancy_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>() : occupancy_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>();
     }
 }
 
 template <typename T>
 int occupancy(int variant, int eos, bool w) {
     switch (variant) {
-        case 0: return occupancy_eos<T, 128, 5>(eos, w);
-        case 1: return occupancy_eos<T, 128, 6>(eos, w);
-        case 2: return occupancy_eos<T, 240, 5>(eos, w);
-        case 3: return occupancy_eos<T, 64, 6>(eos, w);
+        case 0: return occupancy_eos<T, 128, 5, 1>(eos, w);
+        case 1: return occupancy_eos<T, 128, 6, 1>(eos, w);
+        case 2: return occupancy_eos<T, 240, 5, 1>(eos, w);
+        case 3: return occupancy_eos<T, 64, 6, 1>(eos, w);
+        case 4: return occupancy_eos<T, 128, 6, 2>(eos, w);
+        case 5: return occupancy_eos<T, 128, 8, 2>(eos, w);
         default: return 0;
     }
 }
@@ -855,20 +879,20 @@ k_batch_measure(const BatchLattice<T> *__restrict__ lats, int phase,
     if (threadIdx.x < 8) out[blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
 }
 
-template <typename T, int EOS, int TX, int S>
+template <typename T, int EOS, int TX, int S, int G>
 cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void *maps,
                           const void *lats, const BatchItem *items, int n_items, int phase,
                           int *errs, cudaStream_t st) {
-    auto kern = k_batch_step<T, EOS, TX, S>;
-    constexpr size_t smem = step_smem_bytes<T, TX, S>();
+    auto kern = k_batch_step<T, EOS, TX, S, G>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
     if (configure) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, TX / 2, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, G * TX / 2, smem);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(TX / 2);
+    cfg.blockDim = dim3(G * TX / 2);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -881,17 +905,17 @@ cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void
                               errs);
 }
 
-template <typename T, int TX, int S>
+template <typename T, int TX, int S, int G>
 cudaError_t batch_eos(int eos, bool configure, int *occ, int grid, const void *maps,
                       const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
                       cudaStream_t st) {
     switch (eos) {
         case LB_EOS_CS:
-            return batch_variant<T, LB_EOS_CS, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_CS, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
         case LB_EOS_EXP:
-            return batch_variant<T, LB_EOS_EXP, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_EXP, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
         default:
-            return batch_variant<T, LB_EOS_PIECEWISE, TX, S>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_PIECEWISE, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
     }
 }
 
@@ -900,21 +924,23 @@ cudaError_t batch_dispatch(int variant, int eos, bool configure, int *occ, int g
                            const void *maps, const void *lats, const BatchItem *items,
                            int n_items, int phase, int *errs, cudaStream_t st) {
     switch (variant) {
-        case 0: return batch_eos<T, 128, 5>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 1: return batch_eos<T, 128, 6>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 2: return batch_eos<T, 240, 5>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 3: return batch_eos<T, 64, 6>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 0: return batch_eos<T, 128, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 1: return batch_eos<T, 128, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 2: return batch_eos<T, 240, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 3: return batch_eos<T, 64, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 4: return batch_eos<T, 128, 6, 2>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 5: return batch_eos<T, 128, 8, 2>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-int step_variant_count() { return 4; }
+int step_variant_count() { return 6; }
 
 int step_variant_tx(int variant) {
-    static const int tx[] = {128, 128, 240, 64};
-    return (variant >= 0 && variant < 4) ? tx[variant] : 0;
+    static const int tx[] = {128, 128, 240, 64, 128, 128};
+    return (variant >= 0 && variant < 6) ? tx[variant] : 0;
 }
 
 StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
@@ -929,12 +955,12 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
         l.rows = std::min(rows_override, g.ny);
         return l;
     }
-    // about two waves of resident CTAs (measured on GB300 at 2048^2: two waves of 16-row
-    // CTAs beat one wave of 44-row CTAs, the staggered CTA phases overlapping the ring
-    // fill of some with the compute of others), never below 8 rows per CTA
+    // about three waves of resident CTAs (measured on GB300 at 2048^2: 2.7 waves of
+    // 10-row CTAs beat two waves of 14 rows and one wave of 28, the staggered CTA phases
+    // overlapping the ring fill of some with the compute of others), at least 8 rows
     const long long strips = (g.nx + l.tx - 1) / l.tx;
     const long long slots = (long long)std::max(num_sms, 1) * l.ctas_per_sm;
-    long long blocks_y = std::max<long long>(1, 2 * slots / strips);
+    long long blocks_y = std::max<long long>(1, 3 * slots / strips);
     long long rows = (g.ny + blocks_y - 1) / blocks_y;
     rows = std::max<long long>(rows, 8);
     l.rows = (int)std::min<long long>(rows, g.ny);

@@ -31,6 +31,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
+            "lb_autotune",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
@@ -111,6 +112,7 @@ def load_library():
         "lb_maxwell": (I, [C.POINTER(c_lb_eos), D, DP, DP, DP]),
         "lb_launch_variants": (I, []),
         "lb_set_launch": (I, [P, I, I]),
+        "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
         "lb_reduce_noalloc": (I, [P, DP]),
@@ -325,6 +327,13 @@ def lb_set_launch(ctx, variant: int, rows: int = 0):
     _check(load_library().lb_set_launch(ctx, int(variant), int(rows)), "lb_set_launch", ctx)
 
 
+def lb_autotune(ctx, trial_steps: int = 5):
+    v, r = C.c_int(), C.c_int()
+    _check(load_library().lb_autotune(ctx, trial_steps, C.byref(v), C.byref(r)), "lb_autotune",
+           ctx)
+    return v.value, r.value
+
+
 def lb_get_launch(ctx):
     v, tx, rows, occ = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(load_library().lb_get_launch(ctx, C.byref(v), C.byref(tx), C.byref(rows),
@@ -409,6 +418,10 @@ class Lattice:
         return out
 
     # --- time stepping and diagnostics
+    def autotune(self, trial_steps: int = 5):
+        """Pick the fastest step-kernel launch for this lattice (state unchanged)."""
+        return lb_autotune(self.ctx, trial_steps)
+
     def step(self, n: int = 1):
         lb_step(self.ctx, n)
 

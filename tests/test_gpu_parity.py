@@ -323,6 +323,34 @@ def test_every_launch_variant_gives_identical_bits(lbm, prec):
         results.append(outs[0])
 
 
+@pytest.mark.parametrize("walls", [False, True])
+def test_autotune_keeps_the_state_and_the_bits(lbm, walls):
+    """lb_autotune only writes the spare buffer: the state and step count are unchanged,
+    and stepping after it gives the same bits as the default launch."""
+    eos, G, (lo, hi) = case_params(lbm, "cs")
+    rates = lbm.RateParams.from_viscosity(0.1)
+    nx, ny = 517, 203
+    rng = np.random.default_rng(11)
+    rho = I.smooth_random_density(rng, nx, ny, lo, hi)
+    f0 = I.random_populations(rng, rho)
+    outs = []
+    for tune in (False, True):
+        lat = lbm.Lattice(nx, ny, eos, G, kappa=0.3, sigma_force=0.05, rates=rates,
+                          prec="fp32", walls_y=walls)
+        lat.set_populations(f0)
+        lat.step(2)
+        if tune:
+            before = lat.populations()
+            v, r = lat.autotune(2)
+            assert 0 <= v < lbm.lb_launch_variants() and 1 <= r <= ny
+            assert lbm.lb_get_launch(lat.ctx)["variant"] == v
+            assert np.array_equal(lat.populations(), before) and lat.steps_done == 2
+        lat.step(5)
+        outs.append(lat.populations())
+        lat.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_stalled_wait_times_out_and_poisons(lbm):
     """A ring row that is never requested makes the bounded mbarrier wait give up after
     about a second: the step reports LB_ETIMEOUT instead of hanging, and later calls keep
