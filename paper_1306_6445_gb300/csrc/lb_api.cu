@@ -370,8 +370,9 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
             if (seen) continue;
             tried_rows[n_tried++] = rr;
             auto once = [&]() {
-                return lbm::launch_step(c->prec, c->consts, c->geom, c->launch, &c->tmap[c->cur],
-                                        c->f[c->cur ^ 1], c->d_err, c->stream);
+                return lbm::launch_step(c->prec, c->consts, c->geom, c->launch, 0,
+                                        &c->tmap[c->cur], c->f[c->cur ^ 1], c->d_err,
+                                        c->stream);
             };
             e = once();
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -437,8 +438,10 @@ lb_status lb_step(lb_ctx *c, int n) {
     if (s != LB_OK) return s;
     if (n < 0) return fail(c, LB_EINVAL, "lb_step: n < 0");
     for (int i = 0; i < n; ++i) {
-        LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, &c->tmap[c->cur],
-                                    c->f[c->cur ^ 1], c->d_err, c->stream));
+        // alternate the visiting order: each step first reads the rows the previous one
+        // wrote last (still in L2 when the state is not much larger than L2)
+        LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, (int)(c->steps & 1),
+                                    &c->tmap[c->cur], c->f[c->cur ^ 1], c->d_err, c->stream));
         c->cur ^= 1;
         ++c->steps;
     }

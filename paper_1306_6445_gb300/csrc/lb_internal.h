@@ -62,7 +62,8 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
                             int rows_override);
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l);
 // tensor_map_in: a CUtensorMap describing the input buffer (3-D: x, y, population)
-cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l,
+// order 0 / 1: visit the row blocks (and the rows inside them) forward / in reverse
+cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,
                         const void *tensor_map_in, void *gout, int *err, cudaStream_t stream);
 cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf,
                             cudaStream_t stream);

@@ -240,7 +240,8 @@ __device__ __forceinline__ void grid_dependents_launch() {
 
 // One time step for one strip of a lattice: columns x0 .. x0+w-1 (w <= TX, x0 a multiple of
 // 4) and rows yb .. yb+n-1, visited from `start` in direction dir. In the single-lattice
-// kernel dir = +1 for even blockIdx.y and -1 for odd, so that neighbouring row blocks
+// kernel dir = +1 for even row blocks and -1 for odd (reversed on odd time steps, see
+// k_pull_collide), so that neighbouring row blocks
 // reach their shared apron rows at the same time and the second read hits L2.
 //
 // The CTA holds G row groups of TX/2 threads. Iteration k collides the G rows
@@ -456,7 +457,7 @@ template <typename T, int EOS, bool WALLS, int TX, int S, int G>
 __global__ void __launch_bounds__(G * TX / 2)
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<T> P, const int nx, const int ny, const int pitch,
-               const unsigned plane, const int rows, int *__restrict__ err) {
+               const unsigned plane, const int rows, const int order, int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char *smem_raw = align_smem128(smem_dyn);
     if (threadIdx.x == 0) prefetch_tensormap(&tin);
@@ -467,12 +468,16 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     // start its own set-up
     grid_dependency_wait();
     grid_dependents_launch();
-    const int x0 = blockIdx.x * TX;
-    const int yb = blockIdx.y * rows;
+    // order 1 walks the blocks (and the rows inside each block) in reverse: the rows the
+    // previous step wrote last, still in L2, are read first
+    const int bx = order ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int by = order ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int x0 = bx * TX;
+    const int yb = by * rows;
     bool bad = false;
     const int st = march<T, EOS, WALLS, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
                                                min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
-                                               (blockIdx.y & 1) ? -1 : 1, smem_raw, bad);
+                                               ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
     if (bad) atomicOr(err, ERR_DOMAIN);
 }
@@ -740,8 +745,9 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 
 template <typename T, int EOS, bool WALLS, int TX, int S, int G>
-cudaError_t step_variant(const Consts &c, const Geom &g, int rows, const CUtensorMap &tin,
-                         void *out, int *err, cudaStream_t st, bool configure) {
+cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
+                         const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
+                         bool configure) {
     auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
     constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
     if (configure) {
@@ -760,37 +766,37 @@ cudaError_t step_variant(const Consts &c, const Geom &g, int rows, const CUtenso
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, tin, static_cast<T *>(out), to_dev<T>(c), g.nx, g.ny,
-                              g.pitch, (unsigned)g.plane, rows, err);
+                              g.pitch, (unsigned)g.plane, rows, order, err);
 }
 
 template <typename T, int TX, int S, int G>
-cudaError_t step_eos(const Consts &c, const Geom &g, int rows, const CUtensorMap &tin, void *out,
-                     int *err, cudaStream_t st, bool configure) {
+cudaError_t step_eos(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
+                     void *out, int *err, cudaStream_t st, bool configure) {
     const bool w = g.walls != 0;
     switch (c.eos_kind) {
         case LB_EOS_CS:
-            return w ? step_variant<T, LB_EOS_CS, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_CS, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_CS, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_CS, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
         case LB_EOS_EXP:
-            return w ? step_variant<T, LB_EOS_EXP, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_EXP, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_EXP, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_EXP, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
         default:
-            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>(c, g, rows, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>(c, g, rows, tin, out, err, st, configure);
+            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
     }
 }
 
 template <typename T>
-cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l,
+cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l, int order,
                           const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                           bool configure) {
     switch (l.variant) {
-        case 0: return step_eos<T, 128, 5, 1>(c, g, l.rows, tin, out, err, st, configure);
-        case 1: return step_eos<T, 128, 6, 1>(c, g, l.rows, tin, out, err, st, configure);
-        case 2: return step_eos<T, 240, 5, 1>(c, g, l.rows, tin, out, err, st, configure);
-        case 3: return step_eos<T, 64, 6, 1>(c, g, l.rows, tin, out, err, st, configure);
-        case 4: return step_eos<T, 128, 6, 2>(c, g, l.rows, tin, out, err, st, configure);
-        case 5: return step_eos<T, 128, 8, 2>(c, g, l.rows, tin, out, err, st, configure);
+        case 0: return step_eos<T, 128, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 1: return step_eos<T, 128, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 2: return step_eos<T, 240, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 3: return step_eos<T, 64, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 4: return step_eos<T, 128, 6, 2>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 5: return step_eos<T, 128, 8, 2>(c, g, l.rows, order, tin, out, err, st, configure);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -969,15 +975,15 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
 
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l) {
     static const CUtensorMap dummy{};
-    if (prec == LB_FP32) return step_dispatch<float>(c, g, l, dummy, nullptr, nullptr, nullptr, true);
-    return step_dispatch<double>(c, g, l, dummy, nullptr, nullptr, nullptr, true);
+    if (prec == LB_FP32) return step_dispatch<float>(c, g, l, 0, dummy, nullptr, nullptr, nullptr, true);
+    return step_dispatch<double>(c, g, l, 0, dummy, nullptr, nullptr, nullptr, true);
 }
 
-cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l,
+cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,
                         const void *tensor_map_in, void *gout, int *err, cudaStream_t st) {
     const CUtensorMap &tin = *static_cast<const CUtensorMap *>(tensor_map_in);
-    if (prec == LB_FP32) return step_dispatch<float>(c, g, l, tin, gout, err, st, false);
-    return step_dispatch<double>(c, g, l, tin, gout, err, st, false);
+    if (prec == LB_FP32) return step_dispatch<float>(c, g, l, order, tin, gout, err, st, false);
+    return step_dispatch<double>(c, g, l, order, tin, gout, err, st, false);
 }
 
 cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, cudaStream_t st) {
