@@ -42,7 +42,7 @@ METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64 on GB300; batched droplets/s
 NX, NY, INNER = 2048, 2048, 100
 WORKLOAD = ("D2Q9 MRT pseudopotential droplet 2048x2048 periodic, Carnahan-Starling T=0.8Tc, "
             "G=-1, kappa=0.6, nu=0.1, R=200; 100 LB steps + 1 FP64 reduction per bench step")
-ALG_BYTES_PER_SITE = {"fp32": 72, "fp64": 144}   # 9 populations read + 9 written
+ALG_BYTES_PER_SITE = {"fp32": 72, "fp64": 144, "bf16": 36}   # 9 populations read + 9 written
 
 
 def parse():
@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=10000,
                     help="time steps of the 512-lattice batched sweep (0: skip it)")
     ap.add_argument("--batch-lattices", type=int, default=512)
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate leg (converged sweep, training, judged kappa)")
     return ap.parse_args()
@@ -163,7 +164,9 @@ def droplet_setup(lbm, inputs, nx, ny):
 
 def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist, launch=None):
     eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
-    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec)
+    # BF16 storage: shift by the vapour density (most sites of the droplet lattice)
+    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec,
+                      storage_shift=float(rho.min()))
     lat.set_rho_u(rho)
     if launch is not None and launch[0] >= 0:
         lbm.lb_set_launch(lat.ctx, launch[0], launch[1])
@@ -306,6 +309,50 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
     }
 
 
+def bf16_error_table(lbm, inputs, n=256, steps=40000):
+    """Converged n^2 droplet (CS 0.8 T_c, R = 50, nu = 0.1, Maxwell initial densities):
+    density ratio, Laplace surface tension (p_in - p_out) R, max |v| and mass drift in FP32
+    and BF16 storage (rho_s = vapour density) relative to FP64. For the EOS-based potential
+    the pressure rho/3 + (G/2) psi^2 of Eq. 20 is the EOS pressure itself."""
+    import numpy as np
+    eos = lbm.cs_eos(0.8)
+    rates = lbm.RateParams.from_viscosity(0.1)
+    pv, pl, _ = lbm.lb_maxwell(eos, -1.0)
+    rows = {}
+    for prec in ("fp64", "fp32", "bf16"):
+        lat = lbm.Lattice(n, n, eos, -1.0, rates=rates, prec=prec, storage_shift=pv)
+        lat.set_rho_u(inputs.droplet_density(n, n, 50.0, pl, pv))
+        m0 = lat.reduce()
+        lat.step(steps)
+        r = lat.rho()
+        m1 = lat.reduce()
+        lat.close()
+        y, x = np.mgrid[0:n, 0:n]
+        rr = np.hypot(x - (n - 1) / 2, y - (n - 1) / 2)
+        inside, outside = rr < 25.0, rr > 50.0 + 0.3 * n / 2
+        p = p_cs(r, eos)
+        rin, rout = r[inside].mean(), r[outside].mean()
+        R = np.sqrt((r.sum() - rout * r.size) / (np.pi * (rin - rout)))
+        rows[prec] = {"ratio": rin / rout, "theta": (p[inside].mean() - p[outside].mean()) * R,
+                      "umax": m1[3], "mass_drift": (m1[0] - m0[0]) / m0[0]}
+    ref = rows["fp64"]
+    out = {}
+    for prec in ("fp32", "bf16"):
+        r = rows[prec]
+        out[prec] = {"ratio_rel_err": round(r["ratio"] / ref["ratio"] - 1, 5),
+                     "sigma_rel_err": round(r["theta"] / ref["theta"] - 1, 5),
+                     "umax_vs_fp64": round(r["umax"] / ref["umax"], 3),
+                     "mass_drift": float(f"{r['mass_drift']:.3e}")}
+    out["workload"] = f"{n}^2 droplet, CS 0.8Tc, R=50, nu=0.1, {steps} steps, rho_s=rho_v"
+    return out
+
+
+def p_cs(r, eos):
+    """Carnahan-Starling pressure (measurement only; the update runs in the library)."""
+    eta = eos.b * r / 4.0
+    return r * eos.R * eos.T * (1 + eta + eta * eta - eta ** 3) / (1 - eta) ** 3 - eos.a * r * r
+
+
 def surrogate_leg(lbm, torch, n_train=512):
     """The surrogate end to end: a converged batched Laplace sweep of n_train droplets
     (128^2, R = 32, 24000 steps, reading averaged over the last 2048), full-batch Adam
@@ -435,6 +482,17 @@ def native(args):
             "hbm_frac": round(alg64 / (f_kern * 1e-3) / 1e9 / hbm, 4), "launch": shape64,
             "note": "FP64 update is bound by FP64 ALU throughput on GB300, not HBM"}
 
+    # BF16 storage leg: speed, and the error table of a converged droplet against FP64
+    bf16 = None
+    if not args.no_bf16:
+        b_total, b_kern, _, shape16 = time_precision(lbm, torch, inputs, "bf16", nx, ny, inner,
+                                                     max(K // 2, 1), 1, dist)
+        alg16 = ALG_BYTES_PER_SITE["bf16"] * sites
+        bf16 = {"value": round(sites * inner * max(K // 2, 1) / (b_total * 1e-3) / 1e6, 1),
+                "unit": "MLUPS", "kernel_ms": round(b_kern, 5),
+                "hbm_frac": round(alg16 / (b_kern * 1e-3) / 1e9 / hbm, 4), "launch": shape16,
+                "error_vs_fp64": bf16_error_table(lbm, inputs)}
+
     e2e = None
     if not args.no_e2e:
         el, bi, bo = time_e2e(lbm, torch, inputs, nx, ny, inner, K, min(W, 2))
@@ -456,7 +514,8 @@ def native(args):
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"},
             "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks.summary(), "batched": batched,
+            "gpu_launches": launches, "clocks": clocks.summary(), "bf16": bf16,
+            "batched": batched,
             "surrogate": surr,
         }
         print(json.dumps(line), flush=True)

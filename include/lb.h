@@ -18,7 +18,8 @@
  * - Velocities e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
  * - Host field arrays are row-major [y][x] (x fastest), nx * ny doubles, owned by
  *   the caller. Host population arrays are [alpha][y][x], 9 * ny * nx elements of
- *   the context's storage type (double for LB_FP64, float for LB_FP32).
+ *   the context's storage type (double for LB_FP64, float for LB_FP32, and for LB_BF16 the
+ *   16-bit stored patterns of f_a - w_a rho_s, see lb_prec).
  * - Populations are stored on the device as 9 planes of ny rows of `pitch`
  *   elements (pitch = lb_pitch(nx, prec) >= nx + 8, a multiple of 32 elements).
  *   Column x of a row sits at element x + 4; elements 2, 3 and nx+4, nx+5 hold
@@ -52,7 +53,13 @@ typedef enum {
 } lb_status;
 
 typedef enum { LB_EOS_CS = 0, LB_EOS_EXP = 1, LB_EOS_PIECEWISE = 2 } lb_eos_kind;
-typedef enum { LB_FP64 = 0, LB_FP32 = 1 } lb_prec;
+/* Storage / arithmetic precision of a context's populations:
+ *  LB_FP64, LB_FP32: stored and computed in that type;
+ *  LB_BF16: stored as BF16 (round to nearest even) of the FP32 difference f_a - w_a rho_s,
+ *           w = 4/9, 1/9 (a = 1..4), 1/36 (a = 5..8), rho_s set by lb_set_storage_shift
+ *           (default 0); every step decodes f_a = float(stored) + w_a rho_s and computes in
+ *           FP32. Single contexts only (not batches). */
+typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_BF16 = 2 } lb_prec;
 typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS_Y = 1 } lb_bc;
 
 /* Equation of state / pseudopotential (Sec. II; Eq. 23).
@@ -111,6 +118,13 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
 /* Number of compiled variants of the step kernel (strip width x shared-memory ring depth
  * x row groups sharing one ring). */
 int lb_launch_variants(void);
+
+/* rho_s of the LB_BF16 storage shift (stored value = BF16(f_a - w_a rho_s)). Call it before
+ * lb_set_rho_u / lb_set_populations: populations already stored keep their bits and are
+ * read with the new shift. A rho_s near the density of most sites keeps the stored
+ * differences small (BF16 keeps 8 significant bits). Synchronises. Errors: LB_EINVAL for a
+ * context that is not LB_BF16 or a non-finite rho_s. */
+lb_status lb_set_storage_shift(lb_ctx *ctx, double rho_s);
 
 /* Choose the step kernel's variant (0 .. lb_launch_variants()-1) and the number of rows
  * each CTA marches over (rows = 0: about three waves of resident CTAs, at least 8 rows).
@@ -182,7 +196,8 @@ lb_status lb_reduce(lb_ctx *ctx, double out[4]);
  * device looks up the array's device address (cudaGetSymbolAddress), so make that first
  * call before any stream capture. All calls share the array: calls that overlap on the
  * GPU (for example on two streams) race and must be serialised by the caller.
- * Errors: as lb_reduce (LB_EDOMAIN, LB_ENONFINITE poison the context), LB_ECUDA. */
+ * Errors: as lb_reduce (LB_EDOMAIN, LB_ENONFINITE poison the context), LB_ECUDA, and
+ * LB_EINVAL for an LB_BF16 context (use lb_reduce). */
 lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]);
 
 /* Number of time steps taken since lb_set_rho_u. */

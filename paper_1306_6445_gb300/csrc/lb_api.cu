@@ -64,7 +64,7 @@ lb_status cuda_fail(lb_ctx *c, cudaError_t e, const char *where) {
         if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call); \
     } while (0)
 
-size_t elem_size(int prec) { return prec == LB_FP32 ? 4 : 8; }
+size_t elem_size(int prec) { return prec == LB_FP32 ? 4 : (prec == LB_BF16 ? 2 : 8); }
 
 bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
 
@@ -74,7 +74,10 @@ lb_status validate(int nx, int ny, const lb_eos *eos, double G, double kappa, do
     // the step kernel addresses a buffer with 32-bit element offsets (9 planes)
     if (9LL * (long long)lb_pitch(nx, prec) * ny >= (1LL << 32)) { why = "lattice too large"; return LB_EINVAL; }
     if (!eos || !r) { why = "eos and rates must not be NULL"; return LB_EINVAL; }
-    if (prec != LB_FP32 && prec != LB_FP64) { why = "prec must be LB_FP64 or LB_FP32"; return LB_EINVAL; }
+    if (prec != LB_FP32 && prec != LB_FP64 && prec != LB_BF16) {
+        why = "prec must be LB_FP64, LB_FP32 or LB_BF16";
+        return LB_EINVAL;
+    }
     if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y) { why = "bad boundary kind"; return LB_EINVAL; }
     if (!(rate_ok(r->s_rho) && rate_ok(r->s_e) && rate_ok(r->s_zeta) && rate_ok(r->s_j) &&
           rate_ok(r->s_q) && rate_ok(r->s_v))) {
@@ -168,8 +171,9 @@ lb_status make_maps(lb_ctx *c) {
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * c->elem, (cuuint64_t)g.plane * c->elem};
     const cuuint32_t box[3] = {(cuuint32_t)(c->launch.tx + 8), 1, 9};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapDataType dt =
-        c->prec == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const CUtensorMapDataType dt = c->prec == LB_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : c->prec == LB_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     for (int b = 0; b < 2; ++b) {
         CUresult r = enc(&c->tmap[b], dt, 3, c->f[b], dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -399,6 +403,16 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
     if (variant) *variant = best_v;
     if (rows) *rows = best_r;
     return sync_and_check(c);
+}
+
+lb_status lb_set_storage_shift(lb_ctx *c, double rho_s) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (c->prec != LB_BF16) return fail(c, LB_EINVAL, "lb_set_storage_shift: LB_BF16 contexts only");
+    if (!std::isfinite(rho_s)) return fail(c, LB_EINVAL, "lb_set_storage_shift: non-finite rho_s");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->consts.shift_rho = rho_s;
+    return LB_OK;
 }
 
 lb_status lb_debug_stall_row(lb_ctx *c, int row) {

@@ -10,11 +10,20 @@
 // exactly like the scalar operation); in FP64 the two lanes are plain scalar doubles.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "lb_internal.h"
 
 namespace lbm {
+
+// Storage element -> arithmetic type: BF16 storage (LB_BF16) is worked on in FP32.
+template <typename T>
+struct ArithOf { using type = T; };
+template <>
+struct ArithOf<__nv_bfloat16> { using type = float; };
+template <typename T>
+using Arith = typename ArithOf<T>::type;
 
 template <typename T>
 struct DevConsts {
@@ -27,6 +36,8 @@ struct DevConsts {
     // Eq. 17 coefficients per relaxed moment k: (1 - s_k), s_k, (1 - s_k/2) and the source
     // weights 3 s_k / 2 (e, zeta) and -s_v (p_xx, p_xy), rounded once from FP64
     T e_keep, e_half, e_src, z_keep, z_half, z_src, q_keep, q_half, v_keep, v_half, v_src;
+    // storage shift w_a rho_s: LB_BF16 stores f_a - w_a rho_s (zero for FP32 / FP64)
+    T wshift[9];
     int stall_row;
 };
 
@@ -53,6 +64,8 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.z_keep = T(1.0 - c.s_z); d.z_half = T(1.0 - 0.5 * c.s_z); d.z_src = T(1.5 * c.s_z);
     d.q_keep = T(1.0 - c.s_q); d.q_half = T(1.0 - 0.5 * c.s_q);
     d.v_keep = T(1.0 - c.s_v); d.v_half = T(1.0 - 0.5 * c.s_v); d.v_src = T(-c.s_v);
+    for (int a = 0; a < 9; ++a)
+        d.wshift[a] = T((a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0)) * c.shift_rho);
     d.stall_row = c.stall_row;
     return d;
 }
@@ -75,6 +88,24 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---- stored population <-> value. FP32 / FP64 store f itself; LB_BF16 stores the FP32
+// difference f_a - w_a rho_s rounded to BF16 (nearest even), and reads it back exactly
+// as float(stored) + w_a rho_s (one FP32 rounding).
+template <typename T>
+__device__ __forceinline__ Arith<T> pop_dec(T v, int, const DevConsts<Arith<T>> &) { return v; }
+template <>
+__device__ __forceinline__ float pop_dec<__nv_bfloat16>(__nv_bfloat16 v, int a,
+                                                         const DevConsts<float> &P) {
+    return __fadd_rn(__bfloat162float(v), P.wshift[a]);
+}
+template <typename T>
+__device__ __forceinline__ T pop_enc(Arith<T> v, int, const DevConsts<Arith<T>> &) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 pop_enc<__nv_bfloat16>(float v, int a,
+                                                                 const DevConsts<float> &P) {
+    return __float2bfloat16_rn(__fsub_rn(v, P.wshift[a]));
+}
 
 // Interaction potential psi(rho) (Sec. II): psi0 exp(-rho0/rho), or
 // sqrt(2 (p_EOS - rho c_s^2) / G) with p_EOS the Carnahan-Starling EOS or Eq. 23.

@@ -31,6 +31,7 @@ struct Consts {
     double sig_coef;  // 12 sigma G^2 / (tau_e - 1/2): Eq. 8 with |F|^2/psi^2 = G^2 |sum w psi e|^2
     double s_e, s_z, s_q, s_v;  // non-conserved relaxation rates (s_rho, s_j drop out, see kernels)
     int stall_row;  // test hook: the step kernel never requests this ring row (INT_MIN = off)
+    double shift_rho;  // rho_s of the LB_BF16 storage shift f_a - w_a rho_s (0 otherwise)
 };
 
 // Geometry of one lattice's device population buffer.
@@ -62,6 +63,28 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
                             int rows_override);
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l);
 // tensor_map_in: a CUtensorMap describing the input buffer (3-D: x, y, population)
+// per-precision step units (lb_step_f32.cu, lb_step_f64.cu, lb_step_bf16.cu); configure:
+// set the kernel attributes only. tensor_map_in points to a CUtensorMap.
+cudaError_t step_f32(const Consts &c, const Geom &g, const StepLaunch &l, int order,
+                     const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
+                     bool configure);
+cudaError_t step_f64(const Consts &c, const Geom &g, const StepLaunch &l, int order,
+                     const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
+                     bool configure);
+cudaError_t step_bf16(const Consts &c, const Geom &g, const StepLaunch &l, int order,
+                      const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
+                      bool configure);
+int occupancy_f32(int variant, int eos_kind, bool walls);
+int occupancy_f64(int variant, int eos_kind, bool walls);
+int occupancy_bf16(int variant, int eos_kind, bool walls);
+// batched-step units (lb_batch_kernels.cu)
+cudaError_t batch_f32(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
+                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
+                      cudaStream_t st);
+cudaError_t batch_f64(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
+                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
+                      cudaStream_t st);
+
 // order 0 / 1: visit the row blocks (and the rows inside them) forward / in reverse
 cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,
                         const void *tensor_map_in, void *gout, int *err, cudaStream_t stream);

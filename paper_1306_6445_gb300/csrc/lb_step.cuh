@@ -1,0 +1,722 @@
+// Templates of the step kernel shared by the per-precision translation units
+// (lb_step_f32.cu, lb_step_f64.cu, lb_step_bf16.cu, lb_batch_kernels.cu) and the
+// auxiliary kernels (lb_kernels.cu). Everything here has internal linkage; each unit
+// instantiates what it launches.
+//
+// Kernels of the D2Q9 MRT pseudopotential update with the surface-tension source term
+// (Li & Luo, arXiv 1306.6445, Sec. II and IV) for sm_103a.
+//
+// State layout
+// ------------
+// The device buffer holds g with f_a(x, t) = g_a(x - e_a) (the populations of time t are
+// obtained by PULLING from g; where x - e_a lies in a wall, f_a(x) = g_opp(a)(x), half-way
+// bounce-back). A time step reads g, pulls f, collides and writes the post-collision f*
+// at the site itself: that f* is the g of the next step (Eq. 4 is the pull). So every step
+// reads each population once and writes it once, with aligned, site-local stores.
+//
+// Each population plane has ny rows of `pitch` elements. Column x of the lattice lives at
+// element x + GH of its row (GH = 4); elements 2, 3 and nx+4, nx+5 are ghost copies of
+// columns nx-2, nx-1 and 0, 1 (periodic images), rewritten by every kernel that writes g.
+//
+// Hot kernel (k_pull_collide): a CTA owns a strip of TX columns (two per thread) and
+// marches up `rows` rows. Rows of g (9 planes x (TX + 8) columns, i.e. the strip plus a
+// 4-column apron on each side) arrive through a ring of S shared-memory stages fed by
+// 3-D TMA loads (cp.async.bulk.tensor) completing on per-stage mbarriers. From the ring a
+// thread pulls f for its two sites, forms rho and psi (psi is never stored in HBM; a
+// four-row psi ring with one halo column on each side lives in shared memory), then
+// collides (Eqs. 3-8, 17-19) in packed two-lane arithmetic and stores f* as one 8-byte
+// (FP32) or 16-byte (FP64) store per population.
+
+
+
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "lb_device.cuh"
+#include "lb_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int GH = 4;  // ghost columns before column 0 of each row
+constexpr int RED_THREADS = 256;      // reduction blocks (diagnostics, batch measurement)
+constexpr int RED_MAX_BLOCKS = 1024;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Slow path of mbar_wait_bounded: poll until the phase completes or ~1 s has passed.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+// Wait for the phase with the given parity; give up after ~1 s (returns false). The first
+// try is inline: in the steady state the row has landed and no call is made.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------- lattice helpers
+__device__ __forceinline__ int opp(int a) {
+    // 0 -> 0, 1 <-> 3, 2 <-> 4, 5 <-> 7, 6 <-> 8
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
+}
+
+__host__ __device__ constexpr int EXv(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int EYv(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+
+// rho = sum_a f_a, always in this association (the packed pair sum below matches it)
+template <typename T>
+__device__ __forceinline__ T sum9(const T (&v)[9]) {
+    return radd(v[0], radd(radd(radd(v[1], v[3]), radd(v[2], v[4])),
+                           radd(radd(v[5], v[7]), radd(v[6], v[8]))));
+}
+
+// f_a(x, y) pulled from g in global memory (periodic x; periodic y or walls).
+template <typename T, bool WALLS>
+__device__ __forceinline__ T pull_global(const T *__restrict__ g, int a, int x, int y, int nx,
+                                         int ny, int pitch, long long plane) {
+    const int ex = EXv(a), ey = EYv(a);
+    int sy = y - ey;
+    if (WALLS && (sy < 0 || sy >= ny)) return g[opp(a) * plane + (long long)y * pitch + x + GH];
+    if (!WALLS) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+    int sx = x - ex;
+    sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+    return g[a * plane + (long long)sy * pitch + sx + GH];
+}
+
+// the value of f_a(x, y) (decoded from the storage type)
+template <typename T, bool WALLS>
+__device__ __forceinline__ Arith<T> pull_val(const T *__restrict__ g, int a, int x, int y,
+                                             int nx, int ny, int pitch, long long plane,
+                                             const DevConsts<Arith<T>> &P) {
+    // a bounced-back link reads the opposite population, whose storage shift is the same
+    return pop_dec<T>(pull_global<T, WALLS>(g, a, x, y, nx, ny, pitch, plane), a, P);
+}
+
+// ---------------------------------------------------------------- the hot kernel
+
+template <typename T>
+struct Ring {
+    // pointers to the three ring rows holding g rows Y-1, Y, Y+1 (each [9][BW])
+    const T *m, *z, *p;
+};
+
+template <typename T>
+__device__ __forceinline__ V2<T> rho_pair(const V2<T> (&f)[9]) {
+    return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+}
+
+// rows of the psi ring for G row groups: at least 3G + 1 (see march), a power of two
+template <int G>
+__host__ __device__ constexpr int psi_ring_rows() { return G == 1 ? 4 : 8; }
+
+// shared-memory layout of k_pull_collide: S ring stages (each rounded up to 128 bytes),
+// the psi ring, then S mbarriers
+template <typename T, int TX, int S, int G>
+__host__ __device__ constexpr size_t step_bar_offset() {
+    return (size_t)S * (((9u * (TX + 8) * sizeof(T)) + 127u) / 128u * 128u) +
+           (((size_t)psi_ring_rows<G>() * (TX + 4) * sizeof(Arith<T>) + 15u) / 16u * 16u);
+}
+template <typename T, int TX, int S, int G>
+__host__ __device__ constexpr size_t step_smem_bytes() {
+    return step_bar_offset<T, TX, S, G>() + (size_t)S * 8 + 128;   // + room to align the base
+}
+
+template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> { using type = float2; };
+template <>
+struct Vec2Of<double> { using type = double2; };
+
+// an aligned pair of adjacent elements from shared memory
+template <typename T>
+__device__ __forceinline__ V2<T> lds_pair(const T *p) {
+    const typename Vec2Of<T>::type v = *reinterpret_cast<const typename Vec2Of<T>::type *>(p);
+    return V2<T>(v.x, v.y);
+}
+
+// an aligned pair of stored elements from shared memory, decoded (population a)
+template <typename T>
+__device__ __forceinline__ V2<Arith<T>> ring_pair(const T *p, int a,
+                                                  const DevConsts<Arith<T>> &P) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        return V2<float>(v) + V2<float>::all(P.wshift[a]);   // lane-wise as pop_dec
+    } else {
+        return lds_pair<T>(p);
+    }
+}
+
+// f of two sites at ring columns cA, cB (adjacent c, c+1 for a thread's own pair; the two
+// strip-halo columns for the halo pair) pulled from the ring rows r.m, r.z, r.p (lattice
+// rows Y-1, Y, Y+1); bounce-back at the walls. ADJ: cB == cA + 1 with cA even, so the
+// unshifted populations come in one aligned 2-element load. A ring row holds the stored
+// populations; the value of stored plane a is decoded with the shift of population a
+// (a bounced-back link reads the opposite population, whose shift is the same).
+template <typename T, bool WALLS, int BW, bool ADJ>
+__device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, int cA, int cB,
+                                      bool bottom, bool top, const DevConsts<Arith<T>> &P) {
+    using A = Arith<T>;
+    auto two = [&](const T *row, int a, int dc) -> V2<A> {
+        if (ADJ && dc == 0) return ring_pair<T>(row + a * BW + cA, a, P);
+        return V2<A>(pop_dec<T>(row[a * BW + cA + dc], a, P),
+                     pop_dec<T>(row[a * BW + cB + dc], a, P));
+    };
+    f[0] = two(r.z, 0, 0);
+    f[1] = two(r.z, 1, -1);
+    f[3] = two(r.z, 3, 1);
+    if (WALLS && bottom) {   // links from below row 0 are wall links: bounce back
+        f[2] = two(r.z, 4, 0);
+        f[5] = two(r.z, 7, 0);
+        f[6] = two(r.z, 8, 0);
+    } else {
+        f[2] = two(r.m, 2, 0);
+        f[5] = two(r.m, 5, -1);
+        f[6] = two(r.m, 6, 1);
+    }
+    if (WALLS && top) {
+        f[4] = two(r.z, 2, 0);
+        f[7] = two(r.z, 5, 0);
+        f[8] = two(r.z, 6, 0);
+    } else {
+        f[4] = two(r.p, 4, 0);
+        f[7] = two(r.p, 7, 1);
+        f[8] = two(r.p, 8, -1);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(T *p, V2<T> v, bool both);
+template <>
+__device__ __forceinline__ void store_pair<float>(float *p, V2<float> v, bool both) {
+    if (both) *reinterpret_cast<float2 *>(p) = v.v;
+    else p[0] = v.v.x;
+}
+template <>
+__device__ __forceinline__ void store_pair<double>(double *p, V2<double> v, bool both) {
+    if (both) *reinterpret_cast<double2 *>(p) = make_double2(v.x, v.y);
+    else p[0] = v.x;
+}
+
+// stored pair of population a (encoded from its value)
+template <typename T>
+__device__ __forceinline__ void store_pop_pair(T *p, V2<Arith<T>> v, bool both, int a,
+                                               const DevConsts<Arith<T>> &P) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        const V2<float> d = v - V2<float>::all(P.wshift[a]);   // lane-wise as pop_enc
+        if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(d.v);
+        else p[0] = __float2bfloat16_rn(d.lo());
+    } else {
+        store_pair<T>(p, v, both);
+    }
+}
+
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// One time step for one strip of a lattice: columns x0 .. x0+w-1 (w <= TX, x0 a multiple of
+// 4) and rows yb .. yb+n-1, visited from `start` in direction dir. In the single-lattice
+// kernel dir = +1 for even row blocks and -1 for odd (reversed on odd time steps, see
+// k_pull_collide), so that neighbouring row blocks
+// reach their shared apron rows at the same time and the second read hits L2.
+//
+// The CTA holds G row groups of TX/2 threads. Iteration k collides the G rows
+// y_k + g dir (y_k = start + G k dir), group g taking row y_k + g dir, with psi of the rows
+// around it; before that, group g pulls row y_k + (G + g) dir (the row it collides next
+// iteration, kept in registers) and forms its psi. Lattice row start + (j-2) dir is the
+// j-th row requested into the ring (slot j mod S): iteration k reads ring rows
+// G k + G + 1 .. G k + 2G + 2; after its barrier rows up to G k + 2G are dead and their
+// slots receive rows up to G k + 2G + S, i.e. (S - 2) / G iterations ahead of use.
+// Psi of row Y sits in psi-ring row Y mod psi_ring_rows<G>(); a row is written one
+// iteration before the last collision that reads it, and the rows read and written in
+// two consecutive iterations span 3G + 1 rows. With walls, psi of rows -1 and ny is
+// that of rows 0 and ny-1 (the collision reads those rows instead).
+//
+// The caller has initialised the S ring mbarriers (fresh, phase 0) and waited for the
+// previous grid. Returns 0, or ERR_TIMEOUT after a bounded wait gave up (then every copy
+// still in flight has landed, or its own bounded wait gave up too).
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+__device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ gout,
+                                     const DevConsts<Arith<T>> &P, const int nx, const int ny,
+                                     const int pitch, const unsigned plane, const int x0,
+                                     const int w, const int yb, const int n, const int dir,
+                                     unsigned char *smem_raw, bool &bad) {
+    static_assert(G == 1 || G == 2, "one or two row groups");
+    static_assert(S >= G + 4, "ring rows of one iteration plus one row in flight");
+    static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
+    constexpr int NT = TX / 2;      // threads per row group
+    constexpr int BW = TX + 8;      // ring row: columns x0-4 .. x0+TX+3 -> ring col = x - x0 + 4
+    constexpr int RW = TX + 4;      // psi row: columns x0-2 .. x0+TX+1 -> psi col = x - x0 + 2
+    constexpr int PR = psi_ring_rows<G>();
+    constexpr uint32_t STAGE_BYTES = 9u * BW * sizeof(T);
+    constexpr int STAGE_ELEMS = (int)(((STAGE_BYTES + 127u) / 128u) * 128u / sizeof(T));
+    using A = Arith<T>;
+    T *ring = reinterpret_cast<T *>(smem_raw);                 // S stages, 128-byte aligned
+    A *psis = reinterpret_cast<A *>(ring + S * STAGE_ELEMS);    // [PR][RW]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>());
+
+    const int grp = G == 1 ? 0 : (int)threadIdx.x / NT;      // row group
+    const int t = (int)threadIdx.x - grp * NT;                // thread within the group
+    const bool lead = threadIdx.x == 0;                       // requests the ring rows
+    const int c0 = 2 * t;                 // first of the thread's two columns, relative to x0
+    const bool act = c0 < w;
+    const bool both = c0 + 1 < w;
+    const int start = dir > 0 ? yb : yb + n - 1;
+    const int K = (n + G - 1) / G;        // iterations
+    const int nj = G * K + G + 3;         // ring rows j = 0 .. nj-1
+
+    // the lead thread requests ring rows in order
+    int ji = 0, si = 0;
+    auto issue_upto = [&](int jmax) {
+        for (; ji <= jmax && ji < nj; ++ji) {
+            const int r = start + (ji - 2) * dir;
+            const uint32_t sl = (uint32_t)si;
+            si = (si + 1 == S) ? 0 : si + 1;
+            if (r == P.stall_row) continue;   // test hook: the wait for this row must time out
+            // periodic: wrap the row; walls: rows outside the lattice are zero-filled by the
+            // TMA unit and never read (bounce-back replaces those links)
+            const int gy = WALLS ? r : ((r % ny) + ny) % ny;
+            mbar_arrive_expect_tx(&bar[sl], STAGE_BYTES);
+            tma_load_3d(ring + sl * STAGE_ELEMS, tmap, x0, gy, 0, &bar[sl]);
+        }
+    };
+
+    if (lead) issue_upto(S - 1);
+
+    auto stage = [&](int j) -> const T * { return ring + (j % S) * STAGE_ELEMS; };
+    auto wait_row = [&](int j) -> bool {
+        return mbar_wait_bounded(&bar[j % S], (uint32_t)((j / S) & 1));
+    };
+
+    // psi of lattice row Y (ring rows j-1, j, j+1 hold lattice rows Y - dir, Y, Y + dir)
+    // into psi-ring row Y, keeping the pulled populations of the thread's two sites in
+    // `keep`. With walls, rows outside the lattice are skipped (see above).
+    auto psi_row = [&](int Y, int j, V2<A> (&keep)[9]) {
+        if (WALLS && (Y < 0 || Y >= ny)) return;
+        A *ps = psis + (Y & (PR - 1)) * RW;
+        const Ring<T> r = dir > 0 ? Ring<T>{stage(j - 1), stage(j), stage(j + 1)}
+                                  : Ring<T>{stage(j + 1), stage(j), stage(j - 1)};
+        const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
+        if (act) {
+            pull2<T, WALLS, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top, P);
+            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
+            if (both) {
+                store_pair<A>(ps + c0 + 2, psi, true);
+            } else {
+                ps[c0 + 2] = psi.lo();
+            }
+        }
+        if (t == NT - 1) {   // the two halo columns x0-1 and x0+w as one packed pair
+            V2<A> h[9];
+            pull2<T, WALLS, BW, false>(h, r, 3, w + 4, bottom, top, P);
+            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
+            ps[1] = psi.lo();
+            ps[w + 2] = psi.hi();
+        }
+    };
+    // psi-ring row holding psi of lattice row Y (walls: rows -1 and ny read rows 0, ny-1)
+    auto psi_at = [&](int Y) -> const A * {
+        if (WALLS) Y = Y < 0 ? 0 : (Y >= ny ? ny - 1 : Y);
+        return psis + (Y & (PR - 1)) * RW;
+    };
+
+    // prologue: psi of rows start - dir .. start + (G-1) dir from ring rows 0 .. G+2;
+    // group g keeps the populations of row start + g dir (its first collision row).
+    // Group 0 also forms psi(start - dir), after psi(start), in the same threads.
+    bool tmo = false;
+    int jw = 0;                                  // first ring row not yet seen complete
+#pragma unroll 1
+    for (int j = 0; j <= G + 2; ++j) {
+        tmo |= !wait_row(j);
+        if (!tmo) jw = j + 1;
+    }
+    V2<A> fA[9], fB[9];
+    if (!tmo) {
+        psi_row(start + grp * dir, grp + 2, fA);
+        if (grp == 0) psi_row(start - dir, 1, fB);
+    }
+    // ring rows 0 .. G are dead now: refill their slots at once
+    tmo = __syncthreads_or(tmo);
+    if (!tmo && lead) issue_upto(S + G);
+
+    auto body = [&](int k, V2<A> (&fc)[9], V2<A> (&fn)[9]) -> bool {
+        const int y = start + G * k * dir;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int j = G * k + G + 3 + i;
+            if (!tmo) tmo = !wait_row(j);
+            if (!tmo) jw = j + 1;
+        }
+        if (!tmo) psi_row(y + (G + grp) * dir, G * k + G + 2 + grp, fn);
+        if (__syncthreads_or(tmo)) return false;
+        if (lead) issue_upto(G * k + 2 * G + S);   // refill the slots of the dead rows
+
+        const int yr = y + grp * dir;            // this group's collision row
+        if (act && G * k + grp < n) {
+            const A *pm = psi_at(yr - 1);
+            const A *p0 = psi_at(yr);
+            const A *pp = psi_at(yr + 1);
+            const int c = c0 + 2;
+            const V2<A> m0 = lds_pair<A>(pm + c), z0 = lds_pair<A>(p0 + c), q0 = lds_pair<A>(pp + c);
+            const A mL = pm[c - 1], mR = pm[c + 2], zL = p0[c - 1], zR = p0[c + 2];
+            const A qL = pp[c - 1], qR = pp[c + 2];
+            V2<A> pn[9];
+            pn[0] = z0;
+            pn[1] = V2<A>(z0.hi(), zR);
+            pn[2] = q0;
+            pn[3] = V2<A>(zL, z0.lo());
+            pn[4] = m0;
+            pn[5] = V2<A>(q0.hi(), qR);
+            pn[6] = V2<A>(qL, q0.lo());
+            pn[7] = V2<A>(mL, m0.lo());
+            pn[8] = V2<A>(m0.hi(), mR);
+            collide_pair<A>(fc, pn, P);
+
+            const int x = x0 + c0;
+            const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH);
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+                store_pop_pair<T>(gout + (idx + a * plane), fc[a], both, a, P);
+            // ghost images of columns 0, 1 (right of nx-1) and nx-2, nx-1 (left of 0)
+            if (x < 2 || x + 1 >= nx - 2) {
+                const unsigned rowi = (unsigned)yr * (unsigned)pitch;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                    T *rb = gout + (rowi + a * plane);
+                    if (x < 2) rb[nx + GH + x] = v0;
+                    if (both && x + 1 < 2) rb[nx + GH + x + 1] = v1;
+                    if (x >= nx - 2) rb[x - nx + GH] = v0;
+                    if (both && x + 1 >= nx - 2) rb[x + 1 - nx + GH] = v1;
+                }
+            }
+        }
+        return true;
+    };
+
+    int k = 0;
+    bool ok = !tmo;                              // the same in every thread (barrier above)
+    if (ok) {
+        for (; k + 1 < K; k += 2) {
+            if (!body(k, fA, fB) || !body(k + 1, fB, fA)) { ok = false; break; }
+        }
+        if (ok && k < K) ok = body(k, fA, fB);
+    }
+    if (!ok) {
+        // a bounded wait gave up: let every requested copy land (each wait bounded; the
+        // test hook's row was never requested), then leave
+        if (lead)
+            for (int j = jw; j < ji; ++j)
+                if (start + (j - 2) * dir != P.stall_row) (void)wait_row(j);
+        __syncthreads();
+        return ERR_TIMEOUT;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ unsigned char *align_smem128(unsigned char *p) {
+    return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
+template <int S>
+__device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            if (reuse) mbar_inval(&bar[s]);
+            mbar_init(&bar[s], 1);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+__global__ void __launch_bounds__(G * TX / 2)
+k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
+               const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
+               const unsigned plane, const int rows, const int order, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    if (threadIdx.x == 0) prefetch_tensormap(&tin);
+    init_ring_barriers<S>(reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>()),
+                          false);
+    // everything below reads the previous step's output or writes this step's: wait for
+    // the previous grid to complete (programmatic dependent launch), then let the next one
+    // start its own set-up
+    grid_dependency_wait();
+    grid_dependents_launch();
+    // order 1 walks the blocks (and the rows inside each block) in reverse: the rows the
+    // previous step wrote last, still in L2, are read first
+    const int bx = order ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int by = order ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int x0 = bx * TX;
+    const int yb = by * rows;
+    bool bad = false;
+    const int st = march<T, EOS, WALLS, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
+                                               min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
+                                               ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
+    if (threadIdx.x == 0 && st) atomicOr(err, st);
+    if (bad) atomicOr(err, ERR_DOMAIN);
+}
+
+// Many lattices (periodic) in one launch: a persistent grid walks a fixed list of work
+// items (lattice, strip, row block), item i going to CTA i mod gridDim.x. Per-lattice
+// constants, buffers and TMA descriptors come from device tables; `phase` says which of a
+// lattice's two buffers holds the current state. Errors are recorded per lattice.
+template <typename T, int EOS, int TX, int S, int G>
+__global__ void __launch_bounds__(G * TX / 2)
+k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
+             const BatchItem *__restrict__ items, const int n_items, const int phase,
+             int *__restrict__ errs) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + step_bar_offset<T, TX, S, G>());
+    init_ring_barriers<S>(bar, false);
+    grid_dependency_wait();
+    grid_dependents_launch();
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const BatchItem it = items[i];
+        const BatchLattice<T> &L = lats[it.lat];
+        const DevConsts<Arith<T>> P = L.P;
+        const CUtensorMap *map = maps + 2 * it.lat + phase;
+        if (threadIdx.x == 0) prefetch_tensormap(map);
+        bool bad = false;
+        const int st = march<T, EOS, false, TX, S, G>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
+                                                   L.plane, it.x0, it.w, it.yb, it.n, it.dir,
+                                                   smem_raw, bad);
+        if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
+        if (st) {
+            if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
+            return;   // the ring is in an unknown state: this CTA stops
+        }
+        __syncthreads();                 // every thread is done with the ring of this item
+        init_ring_barriers<S>(bar, true);
+    }
+}
+
+// ---------------------------------------------------------------- dispatch
+
+
+
+
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
+                         const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
+                         bool configure) {
+    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    if (configure) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
+    cfg.blockDim = dim3(G * TX / 2);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    // programmatic dependent launch: this grid's CTAs may start their set-up while the
+    // previous step drains; they wait (griddepcontrol.wait) before touching global memory
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tin, static_cast<T *>(out), to_dev<Arith<T>>(c), g.nx, g.ny,
+                              g.pitch, (unsigned)g.plane, rows, order, err);
+}
+
+template <typename T, int TX, int S, int G>
+cudaError_t step_eos(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
+                     void *out, int *err, cudaStream_t st, bool configure) {
+    const bool w = g.walls != 0;
+    switch (c.eos_kind) {
+        case LB_EOS_CS:
+            return w ? step_variant<T, LB_EOS_CS, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_CS, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case LB_EOS_EXP:
+            return w ? step_variant<T, LB_EOS_EXP, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_EXP, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        default:
+            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
+                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+    }
+}
+
+template <typename T>
+cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l, int order,
+                          const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
+                          bool configure) {
+    switch (l.variant) {
+        case 0: return step_eos<T, 128, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 1: return step_eos<T, 128, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 2: return step_eos<T, 240, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        case 3: return step_eos<T, 64, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+int occupancy_variant() {
+    int n = 0;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, G * TX / 2, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <typename T, int TX, int S, int G>
+int occupancy_eos(int eos, bool w) {
+    switch (eos) {
+        case LB_EOS_CS:
+            return w ? occupancy_variant<T, LB_EOS_CS, true, TX, S, G>() : occupancy_variant<T, LB_EOS_CS, false, TX, S, G>();
+        case LB_EOS_EXP:
+            return w ? occupancy_variant<T, LB_EOS_EXP, true, TX, S, G>() : occupancy_variant<T, LB_EOS_EXP, false, TX, S, G>();
+        default:
+            return w ? occupancy_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>() : occupancy_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>();
+    }
+}
+
+template <typename T>
+int occupancy(int variant, int eos, bool w) {
+    switch (variant) {
+        case 0: return occupancy_eos<T, 128, 5, 1>(eos, w);
+        case 1: return occupancy_eos<T, 128, 6, 1>(eos, w);
+        case 2: return occupancy_eos<T, 240, 5, 1>(eos, w);
+        case 3: return occupancy_eos<T, 64, 6, 1>(eos, w);
+        default: return 0;
+    }
+}
+
+template <typename T, int EOS, int TX, int S, int G>
+cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void *maps,
+                          const void *lats, const BatchItem *items, int n_items, int phase,
+                          int *errs, cudaStream_t st) {
+    auto kern = k_batch_step<T, EOS, TX, S, G>;
+    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    if (configure) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, G * TX / 2, smem);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(G * TX / 2);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const CUtensorMap *>(maps),
+                              static_cast<const BatchLattice<T> *>(lats), items, n_items, phase,
+                              errs);
+}
+
+template <typename T, int TX, int S, int G>
+cudaError_t batch_eos(int eos, bool configure, int *occ, int grid, const void *maps,
+                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
+                      cudaStream_t st) {
+    switch (eos) {
+        case LB_EOS_CS:
+            return batch_variant<T, LB_EOS_CS, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case LB_EOS_EXP:
+            return batch_variant<T, LB_EOS_EXP, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        default:
+            return batch_variant<T, LB_EOS_PIECEWISE, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+    }
+}
+
+template <typename T>
+cudaError_t batch_dispatch(int variant, int eos, bool configure, int *occ, int grid,
+                           const void *maps, const void *lats, const BatchItem *items,
+                           int n_items, int phase, int *errs, cudaStream_t st) {
+    switch (variant) {
+        case 0: return batch_eos<T, 128, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 1: return batch_eos<T, 128, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 2: return batch_eos<T, 240, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        case 3: return batch_eos<T, 64, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+}  // namespace lbm

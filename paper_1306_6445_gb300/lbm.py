@@ -22,7 +22,8 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EDOMAIN, LB_ETIMEOUT = 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
                 5: "LB_EDOMAIN", 6: "LB_ETIMEOUT"}
 LB_EOS_CS, LB_EOS_EXP, LB_EOS_PIECEWISE = 0, 1, 2
-LB_FP64, LB_FP32 = 0, 1
+LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
+PRECS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16": LB_BF16}
 LB_BC_PERIODIC, LB_BC_WALLS_Y = 0, 1
 
 # every exported symbol of include/lb.h
@@ -31,7 +32,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
-            "lb_autotune",
+            "lb_autotune", "lb_set_storage_shift",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
@@ -113,6 +114,7 @@ def load_library():
         "lb_launch_variants": (I, []),
         "lb_set_launch": (I, [P, I, I]),
         "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
+        "lb_set_storage_shift": (I, [P, D]),
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
         "lb_reduce_noalloc": (I, [P, DP]),
@@ -334,6 +336,10 @@ def lb_autotune(ctx, trial_steps: int = 5):
     return v.value, r.value
 
 
+def lb_set_storage_shift(ctx, rho_s: float):
+    _check(load_library().lb_set_storage_shift(ctx, float(rho_s)), "lb_set_storage_shift", ctx)
+
+
 def lb_get_launch(ctx):
     v, tx, rows, occ = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(load_library().lb_get_launch(ctx, C.byref(v), C.byref(tx), C.byref(rows),
@@ -381,10 +387,14 @@ class Lattice:
     prec: str = "fp64"
     walls_y: bool = False
     buffers: str = "torch"
+    storage_shift: float = 0.0   # rho_s of prec="bf16" (stored BF16 of f_a - w_a rho_s)
 
     def __post_init__(self):
-        self._prec = LB_FP32 if self.prec == "fp32" else LB_FP64
-        self.dtype = np.float32 if self._prec == LB_FP32 else np.float64
+        if self.prec not in PRECS:
+            raise LBError(LB_EINVAL, "Lattice", f"prec must be one of {sorted(PRECS)}")
+        self._prec = PRECS[self.prec]
+        # host population arrays: float64 / float32, or the raw 16-bit patterns for bf16
+        self.dtype = {LB_FP64: np.float64, LB_FP32: np.float32, LB_BF16: np.uint16}[self._prec]
         bc = LB_BC_WALLS_Y if self.walls_y else LB_BC_PERIODIC
         self._tensors = None
         if self.buffers == "torch":
@@ -401,6 +411,8 @@ class Lattice:
             self.stream = None
             self.ctx = lb_init(self.nx, self.ny, self.eos, self.G, self.kappa, self.sigma_force,
                                self.rates, self._prec, bc, None)
+        if self._prec == LB_BF16:
+            lb_set_storage_shift(self.ctx, self.storage_shift)
 
     # --- state
     def set_rho_u(self, rho, ux=None, uy=None):
@@ -499,6 +511,8 @@ class Batch:
         lib = load_library()
         self.descs = list(descs)
         self.n = len(self.descs)
+        if prec not in ("fp32", "fp64"):
+            raise LBError(LB_EINVAL, "Batch", "batches are fp32 or fp64")
         self._prec = LB_FP32 if prec == "fp32" else LB_FP64
         self.dtype = np.float32 if self._prec == LB_FP32 else np.float64
         arr = (c_lb_lattice_desc * self.n)(*[d.to_c() for d in self.descs])
