@@ -91,6 +91,8 @@ def step(f, params):
     lam = np.diag(np.array([r.s_rho, r.s_e, r.s_zeta, r.s_j, r.s_q, r.s_j, r.s_q, r.s_v, r.s_v],
                            dtype=LD))
     walls = params.walls_y
+    open_bc = getattr(params, "open_bc", False)
+    switch = getattr(params, "visc_switch", None)
 
     rho = np.zeros((ny, nx), dtype=LD)
     for y in range(ny):
@@ -99,10 +101,14 @@ def step(f, params):
     psi = psi_of_rho(rho.astype(np.float64), params.eos, params.G).astype(LD)
 
     def psi_at(x, y):
-        x %= nx
-        if walls:
+        if open_bc:      # nearest lattice site outside (wall row below, open elsewhere)
+            x = min(max(x, 0), nx - 1)
+            y = min(max(y, 0), ny - 1)
+        elif walls:
+            x %= nx
             y = min(max(y, 0), ny - 1)
         else:
+            x %= nx
             y %= ny
         return psi[y, x]
 
@@ -129,6 +135,13 @@ def step(f, params):
 
             fs = f[:, y, x]
             rh = rho[y, x]
+            s_v = LD(r.s_v)
+            if switch is not None and rh < LD(switch[0]):   # nu(rho), Sec. V.C
+                s_v = LD(switch[1])
+            lam_site = lam.copy()
+            lam_site[7, 7] = lam_site[8, 8] = s_v
+            collision_op = M_BF_INV @ lam_site @ M_BF
+            force_op = M_BF_INV @ (np.eye(9, dtype=LD) - lam_site / 2) @ M_BF
             jx = sum(fs[a] * _E[a][0] for a in range(9))
             jy = sum(fs[a] * _E[a][1] for a in range(9))
             vx = (jx + Fx / 2) / rh
@@ -152,10 +165,11 @@ def step(f, params):
             src = np.zeros(9, dtype=LD)
             src[1] = LD(1.5) * LD(r.s_e) * (Qxx + Qyy)
             src[2] = -LD(1.5) * LD(r.s_zeta) * (Qxx + Qyy)
-            src[7] = -LD(r.s_v) * (Qxx - Qyy)
-            src[8] = -LD(r.s_v) * Qxy
+            src[7] = -s_v * (Qxx - Qyy)
+            src[8] = -s_v * Qxy
             post = (fs - collision_op @ (fs - feq) + force_op @ fbar
-                    + M_BF_INV @ ((np.eye(9, dtype=LD) - lam / 2) @ extra) + M_BF_INV @ src)
+                    + M_BF_INV @ ((np.eye(9, dtype=LD) - lam_site / 2) @ extra)
+                    + M_BF_INV @ src)
             fstar[:, y, x] = post
 
     out = np.zeros_like(fstar)
@@ -163,7 +177,12 @@ def step(f, params):
         for y in range(ny):
             for x in range(nx):
                 ys, xs = y - ey, (x - ex) % nx
-                if walls and not (0 <= ys < ny):
+                if open_bc:
+                    if ys < 0:                              # no-slip bottom wall
+                        out[a, y, x] = fstar[_OPP[a], y, x]
+                    else:                                   # open: nearest lattice site
+                        out[a, y, x] = fstar[a, min(ys, ny - 1), min(max(x - ex, 0), nx - 1)]
+                elif walls and not (0 <= ys < ny):
                     out[a, y, x] = fstar[_OPP[a], y, x]
                 else:
                     out[a, y, x] = fstar[a, ys % ny, xs]

@@ -93,6 +93,14 @@ class Params:
     sigma_force: float = 0.0      # the constant sigma of Eq. 8 (not the surface tension)
     rates: Rates = field(default_factory=Rates)
     walls_y: bool = False         # False: periodic in y; True: no-slip walls below y=0 and above y=ny-1
+    # open_bc: no-slip wall below y = 0 and open boundaries (zero-gradient: the missing
+    # neighbour takes the value of the boundary site) above y = ny-1 and beyond x = 0,
+    # x = nx-1, the droplet-splash geometry of Sec. V.C (the paper does not name its open
+    # boundary condition)
+    open_bc: bool = False
+    # nu(rho) of Sec. V.C: (rho_1, s_v used where rho < rho_1); rates.s_v applies where
+    # rho >= rho_1. None: one s_v everywhere.
+    visc_switch: tuple = None
 
 
 # --------------------------------------------------------------------------------------
@@ -104,20 +112,35 @@ def density(f):
     return f.sum(axis=0)
 
 
-def neighbour(field2d, ex: int, ey: int, walls_y: bool):
+def neighbour(field2d, ex: int, ey: int, walls_y: bool, open_bc: bool = False):
     """field(x + ex, y + ey): periodic in x; periodic in y, or with the value of the
-    adjacent fluid row copied into the wall rows y = -1 and y = ny."""
+    adjacent fluid row copied into the wall rows y = -1 and y = ny. With open_bc the value
+    of the nearest lattice site is used outside the lattice in x and y (zero gradient at
+    the open boundaries; the copied wall row below y = 0)."""
+    ny, nx = field2d.shape
+    if open_bc:
+        cols = np.clip(np.arange(nx) + ex, 0, nx - 1)
+        rows = np.clip(np.arange(ny) + ey, 0, ny - 1)
+        return field2d[rows][:, cols]
     out = np.roll(field2d, shift=-ex, axis=1)
     if not walls_y:
         return np.roll(out, shift=-ey, axis=0)
-    ny = field2d.shape[0]
     rows = np.clip(np.arange(ny) + ey, 0, ny - 1)
     return out[rows, :]
 
 
-def neighbour_psi(psi, walls_y: bool):
+def neighbour_psi(psi, walls_y: bool, open_bc: bool = False):
     """[psi(x + e_alpha) for alpha = 0..8]."""
-    return [neighbour(psi, int(EX[a]), int(EY[a]), walls_y) for a in range(9)]
+    return [neighbour(psi, int(EX[a]), int(EY[a]), walls_y, open_bc) for a in range(9)]
+
+
+def viscosity_rate(rho, p):
+    """s_v at every site: rates.s_v, or with nu(rho) (Sec. V.C) the vapour rate where
+    rho < rho_1."""
+    if p.visc_switch is None:
+        return np.full_like(rho, p.rates.s_v)
+    rho1, s_v_vapour = p.visc_switch
+    return np.where(rho >= rho1, p.rates.s_v, s_v_vapour)
 
 
 def interaction_force(psi, psi_nb, G: float):
@@ -186,9 +209,11 @@ def forcing_moments(vx, vy, Fx, Fy, psi, sigma_force: float, s_e: float):
     ])
 
 
-def source_moments(Qxx, Qyy, Qxy, rates: Rates):
-    """C of Eq. 18 (its discrete-lattice correction is already included, Sec. IV)."""
+def source_moments(Qxx, Qyy, Qxy, rates: Rates, s_v=None):
+    """C of Eq. 18 (its discrete-lattice correction is already included, Sec. IV); s_v
+    may be a per-site array (nu(rho))."""
     zero = np.zeros_like(Qxx)
+    s_v = rates.s_v if s_v is None else s_v
     tr = Qxx + Qyy
     return np.stack([
         zero,
@@ -198,24 +223,41 @@ def source_moments(Qxx, Qyy, Qxy, rates: Rates):
         zero,
         zero,
         zero,
-        -rates.s_v * (Qxx - Qyy),
-        -rates.s_v * Qxy,
+        -s_v * (Qxx - Qyy),
+        -s_v * Qxy,
     ])
 
 
-def collide(m, meq, S, C, rates: Rates):
-    """m* = m - Lambda (m - m_eq) + (I - Lambda/2) S + C (Eq. 17, delta_t = 1)."""
-    s = rates.diagonal()[:, None, None]
+def collide(m, meq, S, C, rates: Rates, s_v=None):
+    """m* = m - Lambda (m - m_eq) + (I - Lambda/2) S + C (Eq. 17, delta_t = 1); s_v may
+    be a per-site array (nu(rho)), the other rates are constants."""
+    s = rates.diagonal()[:, None, None] * np.ones_like(m[:1])
+    if s_v is not None:
+        s[7] = s_v
+        s[8] = s_v
     return m - s * (m - meq) + (1.0 - 0.5 * s) * S + C
 
 
-def stream(fstar, walls_y: bool):
+def stream(fstar, walls_y: bool, open_bc: bool = False):
     """f_alpha(x + e_alpha, t + 1) = f*_alpha(x, t) (Eq. 4), written as a pull.
 
     With walls in y (half-way bounce-back): a population that would enter the
     lattice from a wall row is replaced by the opposite population that left the
-    same site toward that wall, f_alpha(x, t + 1) = f*_opp(alpha)(x, t)."""
-    ny = fstar.shape[1]
+    same site toward that wall, f_alpha(x, t + 1) = f*_opp(alpha)(x, t).
+    With open_bc: bounce-back from below y = 0; a population that would enter through
+    an open boundary (above y = ny-1, beyond x = 0 or x = nx-1) is pulled from the
+    nearest lattice site instead (zero gradient)."""
+    ny, nx = fstar.shape[1], fstar.shape[2]
+    if open_bc:
+        out = np.empty_like(fstar)
+        ys, xs = np.mgrid[0:ny, 0:nx]
+        for a in range(9):
+            ex, ey = int(EX[a]), int(EY[a])
+            sy, sx = ys - ey, np.clip(xs - ex, 0, nx - 1)
+            wall = sy < 0
+            sy = np.clip(sy, 0, ny - 1)
+            out[a] = np.where(wall, fstar[OPPOSITE[a]], fstar[a][sy, sx])
+        return out
     out = np.empty_like(fstar)
     for a in range(9):
         ex, ey = int(EX[a]), int(EY[a])
@@ -242,17 +284,18 @@ def step(f, p: Params):
     """One time step f(t) -> f(t + 1): rows a1 .. a9 in order."""
     rho = density(f)                                               # a1
     psi = psi_of_rho(rho, p.eos, p.G)
-    psi_nb = neighbour_psi(psi, p.walls_y)
+    psi_nb = neighbour_psi(psi, p.walls_y, p.open_bc)
     Fx, Fy = interaction_force(psi, psi_nb, p.G)                   # a2
     Qxx, Qyy, Qxy = q_tensor(psi, psi_nb, p.G, p.kappa)            # a3
     vx, vy = velocity(f, rho, Fx, Fy)                              # a4
     m = moments(f)                                                 # a5
     meq = equilibrium_moments(rho, vx, vy)
     S = forcing_moments(vx, vy, Fx, Fy, psi, p.sigma_force, p.rates.s_e)   # a6
-    C = source_moments(Qxx, Qyy, Qxy, p.rates)                     # a7
-    mstar = collide(m, meq, S, C, p.rates)                         # a8
+    s_v = viscosity_rate(rho, p)
+    C = source_moments(Qxx, Qyy, Qxy, p.rates, s_v)                # a7
+    mstar = collide(m, meq, S, C, p.rates, s_v)                    # a8
     fstar = np.tensordot(M_INV, mstar, axes=(1, 0))
-    return stream(fstar, p.walls_y)                                # a9
+    return stream(fstar, p.walls_y, p.open_bc)                     # a9
 
 
 def run(f, p: Params, n: int):
@@ -270,7 +313,7 @@ def macroscopic(f, p: Params):
     """(rho, ux, uy) with the half-force velocity of Eq. 6."""
     rho = density(f)
     psi = psi_of_rho(rho, p.eos, p.G)
-    Fx, Fy = interaction_force(psi, neighbour_psi(psi, p.walls_y), p.G)
+    Fx, Fy = interaction_force(psi, neighbour_psi(psi, p.walls_y, p.open_bc), p.G)
     ux, uy = velocity(f, rho, Fx, Fy)
     return rho, ux, uy
 

@@ -217,3 +217,81 @@ def test_bounce_back_reflects_at_the_wall():
     assert out[7, 2, 0] == 2.0
     assert out[8, 3, 1] == 3.0
     assert out.sum() == 6.0
+
+
+# ---------------------------------------------------------------- splash geometry (Sec. V.C)
+
+def splash_params(case, switch=True):
+    eos, G, kappa, sigma, (lo, hi) = CASES[case]
+    rates = L.Rates(s_rho=1.0, s_e=0.8, s_zeta=0.8, s_j=1.0, s_q=1.1, s_v=1.6)
+    sw = (0.5 * (lo + hi), 0.9) if switch else None
+    return L.Params(eos=eos, G=G, kappa=kappa, sigma_force=sigma, rates=rates, open_bc=True,
+                    visc_switch=sw), (lo, hi)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_open_boundaries_and_viscosity_switch_equal_bruteforce_twin(case):
+    p, (lo, hi) = splash_params(case)
+    rng = np.random.default_rng(40 + case)
+    rho = I.smooth_random_density(rng, 8, 7, lo, hi)
+    f = I.random_populations(rng, rho)
+    a = L.step(f, p)
+    b = BF.step(f, p).astype(np.float64)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+    a = L.run(f, p, 20)
+    b = BF.run(f, p, 20).astype(np.float64)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_viscosity_switch_limits_are_the_plain_rates():
+    """rho_1 below every density: the liquid rate everywhere; above every density: the
+    vapour rate everywhere."""
+    p, (lo, hi) = splash_params(0)
+    rng = np.random.default_rng(7)
+    rho = I.smooth_random_density(rng, 16, 12, lo, hi)
+    f = I.random_populations(rng, rho)
+    low = L.Params(**{**p.__dict__, "visc_switch": (0.5 * lo, 0.9)})
+    high = L.Params(**{**p.__dict__, "visc_switch": (2.0 * hi, 0.9)})
+    liquid = L.Params(**{**p.__dict__, "visc_switch": None})
+    vapour = L.Params(**{**p.__dict__, "visc_switch": None,
+                         "rates": L.Rates(**{**p.rates.__dict__, "s_v": 0.9})})
+    assert np.array_equal(L.step(f, low), L.step(f, liquid))
+    assert np.array_equal(L.step(f, high), L.step(f, vapour))
+    assert not np.allclose(L.step(f, p), L.step(f, liquid))
+
+
+def test_open_boundary_rest_state_is_stationary():
+    eos = E.cs_eos(0.8)
+    f = L.equilibrium(np.full((9, 11), 0.2), np.zeros((9, 11)), np.zeros((9, 11)))
+    p = L.Params(eos=eos, G=-1.0, kappa=0.3, open_bc=True, visc_switch=(0.1, 0.9))
+    assert np.abs(L.run(f, p, 50) - f).max() < 1e-15
+
+
+def test_open_sides_equal_periodic_for_states_uniform_in_x():
+    """Zero-gradient side boundaries see the same neighbour values as periodic ones when
+    nothing depends on x; the top row then differs only through the open top."""
+    eos = E.cs_eos(0.8)
+    rv, rl, _ = E.mechanical_stability(eos, -1.0)
+    ny, nx = 24, 10
+    rho = I.layer_density(nx, ny, 10.0, rl, rv, width=3.0)
+    f = L.equilibrium(rho, 0 * rho, 0 * rho)
+    p_open = L.Params(eos=eos, G=-1.0, kappa=0.5, open_bc=True)
+    p_walls = L.Params(eos=eos, G=-1.0, kappa=0.5, walls_y=True)
+    a = L.run(f, p_open, 5)
+    b = L.run(f, p_walls, 5)
+    assert np.allclose(a, a[:, :, :1], atol=1e-15, rtol=0)       # stays uniform in x
+    # one step reaches two rows (pull, then psi of the neighbours): after 5 steps the rows
+    # more than 10 below the top, where open and wall boundaries differ, agree to round-off
+    assert np.abs(a[:, :ny - 11] - b[:, :ny - 11]).max() < 1e-13
+    assert np.abs(a[:, ny - 1] - b[:, ny - 1]).max() > 1e-10   # the boundaries do differ
+
+
+def test_open_boundary_pull_copies_the_nearest_site():
+    f = np.zeros((9, 4, 5))
+    f[1, 2, 0] = 1.0           # +x population at the left column: also pulled into x = 0
+    f[4, 3, 2] = 2.0           # -y population at the top row: pulled from the top row itself
+    f[4, 0, 3] = 5.0           # -y population at the bottom row: bounced back as +y
+    out = L.stream(f, walls_y=False, open_bc=True)
+    assert out[1, 2, 0] == 1.0 and out[1, 2, 1] == 1.0
+    assert out[4, 3, 2] == 2.0 and out[4, 2, 2] == 2.0
+    assert out[2, 0, 3] == 5.0
