@@ -64,6 +64,8 @@ def parse():
                     help="time steps of the 512-lattice batched sweep (0: skip it)")
     ap.add_argument("--batch-lattices", type=int, default=512)
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
+    ap.add_argument("--no-splash", action="store_true", help="skip the splash leg")
+    ap.add_argument("--splash-steps", type=int, default=40000)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate leg (converged sweep, training, judged kappa)")
     return ap.parse_args()
@@ -381,9 +383,8 @@ def surrogate_leg(lbm, torch, n_train=512):
     res = surrogate.tune_kappa(lbm, net, g[:, 0], g[:, 1], g[:, 2], tol=0.02, max_rounds=0)
     s0 = surrogate.sweep_points(lbm, g[:, 0], np.zeros(len(g)), g[:, 1])
     s_law = surrogate.sweep_points(lbm, g[:, 0], 1 - g[:, 2] / s0, g[:, 1])
-    net.close()
     e_net, e_law = np.abs(res["rel_err"]), np.abs(s_law / g[:, 2] - 1)
-    return {
+    return net, {
         "train_samples": int(ok.sum()), "sweep_seconds": round(t_sweep, 3),
         "sweep_droplets_per_s": round(n_train / t_sweep, 1),
         "fit_seconds": round(t_fit, 3), "adam_steps": adam_steps,
@@ -395,6 +396,61 @@ def surrogate_leg(lbm, torch, n_train=512):
         "sigma_err_law_max": round(float(e_law.max()), 5),
         "law_calibration_runs_per_target": 1,
     }
+
+
+def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, We=200.0, Re=500.0, U=0.05,
+               t_over_tc=0.65, steps=None):
+    """Droplet splashing on a thin film at 4096 x 1024 (film 0.1 D, D = 400), FP32, CS at
+    0.65 T_c with sigma_F = 0.087, U = 0.05; Re = U D / nu_L, nu_V = 20 nu_L switched at
+    the mean phase density; the target surface tension follows from We = rho_L U^2 D /
+    sigma, and kappa comes from the surrogate network, judged by one Laplace run
+    (128^2). Reports the kernel rate and the spread radius."""
+    import numpy as np
+    from paper_1306_6445_gb300 import splash, surrogate
+
+    steps = ARGS.splash_steps if steps is None else steps
+    eos = lbm.cs_eos(t_over_tc)
+    rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
+    sigma_t = rl * U * U * D / We
+    nu_l = U * D / Re
+    tau_l = 3.0 * nu_l + 0.5
+    res = surrogate.tune_kappa(lbm, net, t_over_tc, tau_l, sigma_t, tol=0.02, max_rounds=2)
+    kappa = float(res["kappa"][0])
+    film = 0.1 * D
+    lat = splash.make_lattice(lbm, nx, ny, eos, -1.0, kappa, 0.087, D, film, U, nu_l,
+                              20.0 * nu_l, 0.5 * (rl + rv), rl, rv)
+    lat.autotune(3)
+    stream = torch.cuda.current_stream()
+    marks = {int(round(t * D / U)): t for t in (0.25, 0.75, 1.0, 1.5, 1.75)}
+    radii = {}
+    done, failed, ms = 0, None, 0.0
+    torch.cuda.synchronize()
+    try:
+        for k in range(0, steps, 1000):
+            n = min(1000, steps - k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(n)
+            e1.record(stream)
+            lat.sync()                      # an EOS-domain error surfaces here
+            ms += e0.elapsed_time(e1)
+            done = k + n
+            if done in marks:
+                radii[marks[done]] = round(splash.spread_radius(lat.rho(), film, D, rl, rv), 4)
+    except lbm.LBError as e:
+        failed = f"{lbm.STATUS_NAMES.get(e.status, e.status)} between steps {done} and {done + 1000}"
+    launch = lbm.lb_get_launch(lat.ctx)
+    lat.close()
+    return {"workload": f"{nx}x{ny} splash, D={D:.0f}, film {film:.0f}, CS {t_over_tc}Tc, "
+                        f"We={We:.0f}, Re={Re:.0f}, U={U}, FP32, {steps} steps",
+            "kappa_from_surrogate": round(kappa, 5), "sigma_target": sigma_t,
+            "sigma_judged_rel_err": round(float(res["rel_err"][0]), 5),
+            "laplace_runs": int(res["runs"][0]),
+            "mlups": round(nx * ny * done / (ms * 1e-3) / 1e6, 1) if done else None,
+            "steps_done": done, "failed": failed, "launch": launch,
+            "t_star_end": round(U * done / D, 3),
+            "spread_radius_over_D_at_t_star": radii,
+            "power_law_1p3_sqrt_t": {t: round(1.3 * t ** 0.5, 4) for t in radii}}
 
 
 def cpu_baseline(nx, ny, budget_s=20.0):
@@ -502,7 +558,12 @@ def native(args):
     batched = None
     if args.batch_steps > 0:
         batched = batched_sweep(lbm, torch, inputs, args.batch_lattices, args.batch_steps)
-    surr = None if args.no_surrogate else surrogate_leg(lbm, torch)
+    surr = splash = None
+    if not args.no_surrogate:
+        net, surr = surrogate_leg(lbm, torch)
+        if not args.no_splash:
+            splash = splash_leg(lbm, torch, net)
+        net.close()
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(nx, ny)
         line = {
@@ -516,7 +577,7 @@ def native(args):
             "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "bf16": bf16,
             "batched": batched,
-            "surrogate": surr,
+            "surrogate": surr, "splash": splash,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -573,8 +634,13 @@ def reference(args):
     }), flush=True)
 
 
+ARGS = None
+
+
 def main():
+    global ARGS
     args = parse()
+    ARGS = args
     if args.impl == "reference":
         reference(args)
     else:

@@ -60,7 +60,14 @@ typedef enum { LB_EOS_CS = 0, LB_EOS_EXP = 1, LB_EOS_PIECEWISE = 2 } lb_eos_kind
  *           (default 0); every step decodes f_a = float(stored) + w_a rho_s and computes in
  *           FP32. Single contexts only (not batches). */
 typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_BF16 = 2 } lb_prec;
-typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS_Y = 1 } lb_bc;
+/* Boundaries: LB_BC_PERIODIC in x and y; LB_BC_WALLS_Y periodic in x with half-way
+ * bounce-back (no-slip) walls below row 0 and above row ny-1 (Sec. V.B); LB_BC_OPEN a
+ * bounce-back wall below row 0 and open boundaries above row ny-1 and beyond columns 0 and
+ * nx-1, where a population entering the lattice is taken from the nearest lattice site
+ * (zero gradient), and psi outside the lattice is that of the nearest site: the
+ * droplet-splash geometry of Sec. V.C, whose open condition the paper does not name.
+ * LB_BC_OPEN is compiled for LB_FP32 and LB_FP64 and supports lb_set_viscosity_switch. */
+typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS_Y = 1, LB_BC_OPEN = 2 } lb_bc;
 
 /* Equation of state / pseudopotential (Sec. II; Eq. 23).
  *  LB_EOS_CS:        p = rho R T (1 + eta + eta^2 - eta^3)/(1 - eta)^3 - a rho^2, eta = b rho/4;
@@ -118,6 +125,13 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
 /* Number of compiled variants of the step kernel (strip width x shared-memory ring depth
  * x row groups sharing one ring). */
 int lb_launch_variants(void);
+
+/* Density-dependent viscosity of Sec. V.C (LB_BC_OPEN contexts): sites with rho < rho_1
+ * relax the viscous moments p_xx, p_xy at s_v_vapour (the vapour viscosity
+ * (1/s_v_vapour - 1/2)/3), the others at the context's s_v; rho is the site density of
+ * the step (Eq. 6). Off until called. Synchronises. Errors: LB_EINVAL for another boundary
+ * kind, a non-finite rho_1 or s_v_vapour outside (0, 2). */
+lb_status lb_set_viscosity_switch(lb_ctx *ctx, double rho_1, double s_v_vapour);
 
 /* rho_s of the LB_BF16 storage shift (stored value = BF16(f_a - w_a rho_s)). Call it before
  * lb_set_rho_u / lb_set_populations: populations already stored keep their bits and are

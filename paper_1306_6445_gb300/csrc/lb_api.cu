@@ -78,7 +78,14 @@ lb_status validate(int nx, int ny, const lb_eos *eos, double G, double kappa, do
         why = "prec must be LB_FP64, LB_FP32 or LB_BF16";
         return LB_EINVAL;
     }
-    if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y) { why = "bad boundary kind"; return LB_EINVAL; }
+    if (bc != LB_BC_PERIODIC && bc != LB_BC_WALLS_Y && bc != LB_BC_OPEN) {
+        why = "bad boundary kind";
+        return LB_EINVAL;
+    }
+    if (bc == LB_BC_OPEN && prec == LB_BF16) {
+        why = "open boundaries are compiled for LB_FP32 and LB_FP64";
+        return LB_EINVAL;
+    }
     if (!(rate_ok(r->s_rho) && rate_ok(r->s_e) && rate_ok(r->s_zeta) && rate_ok(r->s_j) &&
           rate_ok(r->s_q) && rate_ok(r->s_v))) {
         why = "relaxation rates must lie in (0, 2) (tau > 1/2)";
@@ -138,6 +145,8 @@ Consts make_consts(const lb_eos *e, double G, double kappa, double sigma, const 
     c.s_q = r->s_q;
     c.s_v = r->s_v;
     c.stall_row = INT_MIN;
+    c.rho_sw = -HUGE_VAL;       // nu(rho) off
+    c.s_v_vapour = c.s_v;
     return c;
 }
 
@@ -247,7 +256,7 @@ lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, doub
     c->geom.ny = ny;
     c->geom.pitch = (int)lb_pitch(nx, prec);
     c->geom.plane = (long long)ny * c->geom.pitch;
-    c->geom.walls = (bc == LB_BC_WALLS_Y) ? 1 : 0;
+    c->geom.walls = bc;   // the boundary kind
     c->consts = make_consts(eos, G, kappa, sigma, rates);
     c->stream = static_cast<cudaStream_t>(stream);
     int dev = 0;
@@ -403,6 +412,19 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
     if (variant) *variant = best_v;
     if (rows) *rows = best_r;
     return sync_and_check(c);
+}
+
+lb_status lb_set_viscosity_switch(lb_ctx *c, double rho_1, double s_v_vapour) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (c->geom.walls != LB_BC_OPEN)
+        return fail(c, LB_EINVAL, "lb_set_viscosity_switch: LB_BC_OPEN contexts only");
+    if (!(std::isfinite(rho_1) && rate_ok(s_v_vapour)))
+        return fail(c, LB_EINVAL, "lb_set_viscosity_switch: need a finite rho_1 and s_v in (0, 2)");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->consts.rho_sw = rho_1;
+    c->consts.s_v_vapour = s_v_vapour;
+    return LB_OK;
 }
 
 lb_status lb_set_storage_shift(lb_ctx *c, double rho_s) {

@@ -322,6 +322,8 @@ lb_status lb_batch_create(lb_batch **out, int n, const lb_lattice_desc *descs, i
         c.s_q = d.rates.s_q;
         c.s_v = d.rates.s_v;
         c.stall_row = INT_MIN;
+        c.rho_sw = -HUGE_VAL;       // nu(rho) off
+        c.s_v_vapour = c.s_v;
         b->consts.push_back(c);
         const size_t bytes = (lb_buffer_bytes(d.nx, d.ny, prec) + 255) / 256 * 256;
         for (int w = 0; w < 2; ++w) {

@@ -38,6 +38,9 @@ struct DevConsts {
     T e_keep, e_half, e_src, z_keep, z_half, z_src, q_keep, q_half, v_keep, v_half, v_src;
     // storage shift w_a rho_s: LB_BF16 stores f_a - w_a rho_s (zero for FP32 / FP64)
     T wshift[9];
+    // nu(rho) (open-boundary kernels only): sites with rho < rho_sw relax p_xx, p_xy at
+    // s_vV; the Eq. 17 coefficients for that rate
+    T rho_sw, s_vV, v_keep_V, v_half_V, v_src_V;
     int stall_row;
 };
 
@@ -66,6 +69,11 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.v_keep = T(1.0 - c.s_v); d.v_half = T(1.0 - 0.5 * c.s_v); d.v_src = T(-c.s_v);
     for (int a = 0; a < 9; ++a)
         d.wshift[a] = T((a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0)) * c.shift_rho);
+    d.rho_sw = T(c.rho_sw);
+    d.s_vV = T(c.s_v_vapour);
+    d.v_keep_V = T(1.0 - c.s_v_vapour);
+    d.v_half_V = T(1.0 - 0.5 * c.s_v_vapour);
+    d.v_src_V = T(-c.s_v_vapour);
     d.stall_row = c.stall_row;
     return d;
 }
@@ -221,7 +229,9 @@ __device__ __forceinline__ V2<T> eos_psi2(V2<T> rho, const DevConsts<T> &P, bool
 //   m*_rho = rho and m*_j = j + F for every s_j (relaxing j towards rho v = j + F/2 and
 //   adding (1 - s_j/2) F cancels s_j exactly), so s_rho and s_j drop out;
 //   m*_k = (1 - s_k) m_k + s_k m_eq_k + (1 - s_k/2) S_k + C_k for the other moments.
-template <typename T>
+//   VSW: nu(rho) of Sec. V.C, the rate of p_xx, p_xy (and the weight of their source
+//   terms) taken per site as s_v where rho >= rho_sw, else s_vV.
+template <typename T, bool VSW = false>
 __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9],
                                              const DevConsts<T> &P) {
     using V = V2<T>;
@@ -290,10 +300,17 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V ms4 = vfma(V::all(P.q_keep), m4, V::all(T(0)) - vfma(V::all(P.s_q), rvx, V::all(P.q_half) * Fx));
     const V ms5 = jy + Fy;
     const V ms6 = vfma(V::all(P.q_keep), m6, V::all(T(0)) - vfma(V::all(P.s_q), rvy, V::all(P.q_half) * Fy));
-    const V ms7 = vfma(V::all(P.v_keep), m7, vfma(V::all(P.s_v), meq7,
-                  vfma(V::all(P.v_half), S7, V::all(P.v_src) * (Qxx - Qyy))));
-    const V ms8 = vfma(V::all(P.v_keep), m8, vfma(V::all(P.s_v), meq8,
-                  vfma(V::all(P.v_half), S8, V::all(P.v_src) * Qxy)));
+    V vkeep = V::all(P.v_keep), vs = V::all(P.s_v), vhalf = V::all(P.v_half);
+    V vsrc = V::all(P.v_src);
+    if constexpr (VSW) {
+        const bool lo = rho.lo() >= P.rho_sw, hi = rho.hi() >= P.rho_sw;
+        vkeep = V(lo ? P.v_keep : P.v_keep_V, hi ? P.v_keep : P.v_keep_V);
+        vs = V(lo ? P.s_v : P.s_vV, hi ? P.s_v : P.s_vV);
+        vhalf = V(lo ? P.v_half : P.v_half_V, hi ? P.v_half : P.v_half_V);
+        vsrc = V(lo ? P.v_src : P.v_src_V, hi ? P.v_src : P.v_src_V);
+    }
+    const V ms7 = vfma(vkeep, m7, vfma(vs, meq7, vfma(vhalf, S7, vsrc * (Qxx - Qyy))));
+    const V ms8 = vfma(vkeep, m8, vfma(vs, meq8, vfma(vhalf, S8, vsrc * Qxy)));
 
     // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
     const V c9 = V::all(T(1.0 / 9.0)), c18 = V::all(T(1.0 / 18.0)), c36 = V::all(T(1.0 / 36.0));

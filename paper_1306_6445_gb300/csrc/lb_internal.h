@@ -32,6 +32,8 @@ struct Consts {
     double s_e, s_z, s_q, s_v;  // non-conserved relaxation rates (s_rho, s_j drop out, see kernels)
     int stall_row;  // test hook: the step kernel never requests this ring row (INT_MIN = off)
     double shift_rho;  // rho_s of the LB_BF16 storage shift f_a - w_a rho_s (0 otherwise)
+    // nu(rho) of the open-boundary kernels: s_v_vapour where rho < rho_sw (-inf: off)
+    double rho_sw, s_v_vapour;
 };
 
 // Geometry of one lattice's device population buffer.
@@ -39,7 +41,7 @@ struct Geom {
     int nx, ny;
     int pitch;          // elements per stored row (>= nx + 2 * kGhost, multiple of 32)
     long long plane;    // elements per population plane = ny * pitch
-    int walls;          // 0 periodic in y, 1 bounce-back walls in y
+    int walls;          // boundary kind (lb_bc): 0 periodic, 1 walls in y, 2 open (see lb.h)
 };
 
 // One work item of the batched step: a strip of one lattice.
@@ -74,9 +76,9 @@ cudaError_t step_f64(const Consts &c, const Geom &g, const StepLaunch &l, int or
 cudaError_t step_bf16(const Consts &c, const Geom &g, const StepLaunch &l, int order,
                       const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
                       bool configure);
-int occupancy_f32(int variant, int eos_kind, bool walls);
-int occupancy_f64(int variant, int eos_kind, bool walls);
-int occupancy_bf16(int variant, int eos_kind, bool walls);
+int occupancy_f32(int variant, int eos_kind, int bc);
+int occupancy_f64(int variant, int eos_kind, int bc);
+int occupancy_bf16(int variant, int eos_kind, int bc);
 // batched-step units (lb_batch_kernels.cu)
 cudaError_t batch_f32(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
                       const void *lats, const BatchItem *items, int n_items, int phase, int *errs,

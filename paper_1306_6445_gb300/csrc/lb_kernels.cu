@@ -9,11 +9,21 @@ namespace {
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// launch X(T, BC) for the geometry's boundary kind
+#define BC3(X, T)                       \
+    do {                                \
+        if (g.walls == 2) X(T, 2);      \
+        else if (g.walls == 1) X(T, 1); \
+        else X(T, 0);                   \
+    } while (0)
+
 // ---------------------------------------------------------------- permutations
 
-// g_b(y) = f_b(y + e_b) where y + e_b is inside the lattice, else f_opp(b)(y) (inverse of
-// the pull with bounce-back). f and g use the padded layout; ghosts of g are written.
-template <typename T, bool WALLS>
+// g_b(y) = f_b(y + e_b) where y + e_b is inside the lattice, else f_opp(b)(y) at a wall
+// (inverse of the pull with bounce-back); a population leaving through an open boundary
+// (BC 2) is not pulled back by any site and keeps f_b(y). f and g use the padded layout;
+// the ghost columns of g are written (periodic images, or copies of the edge columns).
+template <typename T, int BC>
 __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, int ny, int pitch,
                            long long plane) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -21,25 +31,31 @@ __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, i
     const int y = (int)(i / nx), x = (int)(i % nx);
 #pragma unroll
     for (int b = 0; b < 9; ++b) {
-        int ty = y + EYv(b);
+        int ty = y + EYv(b), tx = x + EXv(b);
         T v;
-        if (WALLS && (ty < 0 || ty >= ny)) {
+        if ((BC != 0 && ty < 0) || (BC == 1 && ty >= ny)) {
             v = f[opp(b) * plane + (long long)y * pitch + x + GH];
+        } else if (BC == 2 && (ty >= ny || tx < 0 || tx >= nx)) {
+            v = f[b * plane + (long long)y * pitch + x + GH];
         } else {
-            if (!WALLS) ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-            int tx = x + EXv(b);
+            if (BC == 0) ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
             tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
             v = f[b * plane + (long long)ty * pitch + tx + GH];
         }
         T *rowg = g + b * plane + (long long)y * pitch;
         rowg[x + GH] = v;
-        if (x < 2) rowg[nx + GH + x] = v;
-        if (x >= nx - 2) rowg[x - nx + GH] = v;
+        if (BC == 2) {
+            if (x == 0) rowg[GH - 1] = rowg[GH - 2] = v;
+            if (x == nx - 1) rowg[nx + GH] = rowg[nx + GH + 1] = v;
+        } else {
+            if (x < 2) rowg[nx + GH + x] = v;
+            if (x >= nx - 2) rowg[x - nx + GH] = v;
+        }
     }
 }
 
 // f_a(x) = pull of g (the populations of the current time), padded layout, no ghosts.
-template <typename T, bool WALLS>
+template <typename T, int BC>
 __global__ void k_stream(const T *__restrict__ g, T *__restrict__ f, int nx, int ny, int pitch,
                          long long plane) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,7 +64,7 @@ __global__ void k_stream(const T *__restrict__ g, T *__restrict__ f, int nx, int
 #pragma unroll
     for (int a = 0; a < 9; ++a)
         f[a * plane + (long long)y * pitch + x + GH] =
-            pull_global<T, WALLS>(g, a, x, y, nx, ny, pitch, plane);
+            pull_global<T, BC>(g, a, x, y, nx, ny, pitch, plane);
 }
 
 // f = M^-1 m_eq(rho, u) (Eq. 3) at every site, computed in double, in the padded layout.
@@ -90,7 +106,7 @@ __global__ void k_init_feq(const double *__restrict__ rho, const double *__restr
 // ---------------------------------------------------------------- diagnostics
 
 // psi(rho(x)) in the arithmetic type, into a packed nx*ny array.
-template <typename T, int EOS, bool WALLS>
+template <typename T, int EOS, int BC>
 __global__ void k_psi_field(const T *__restrict__ g, Arith<T> *__restrict__ psi,
                             const DevConsts<Arith<T>> P, int nx, int ny, int pitch,
                             long long plane, int *__restrict__ err) {
@@ -99,27 +115,31 @@ __global__ void k_psi_field(const T *__restrict__ g, Arith<T> *__restrict__ psi,
     const int y = (int)(i / nx), x = (int)(i % nx);
     Arith<T> v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pull_val<T, WALLS>(g, a, x, y, nx, ny, pitch, plane, P);
+    for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, y, nx, ny, pitch, plane, P);
     bool bad = false;
     psi[i] = eos_psi<Arith<T>, EOS>(sum9(v), P, bad);
     if (bad) atomicOr(err, ERR_DOMAIN);
 }
 
 // rho and v = (sum e f + F/2)/rho (Eq. 6) of one site, from g and the psi field.
-template <typename T, bool WALLS, typename A = Arith<T>>
+template <typename T, int BC, typename A = Arith<T>>
 __device__ __forceinline__ void site_macro(const T *__restrict__ g, const A *__restrict__ psi,
                                            const DevConsts<A> &P, int nx, int ny, int pitch,
                                            long long plane, int x, int y, A &rho, A &vx, A &vy) {
     const A G = P.G;
     A v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pull_val<T, WALLS>(g, a, x, y, nx, ny, pitch, plane, P);
+    for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, y, nx, ny, pitch, plane, P);
     rho = sum9(v);
     const A jx = (v[1] - v[3]) + (v[5] - v[7]) - (v[6] - v[8]);
     const A jy = (v[2] - v[4]) + (v[5] - v[7]) + (v[6] - v[8]);
-    const int xp = (x + 1 == nx) ? 0 : x + 1, xm = (x == 0) ? nx - 1 : x - 1;
+    int xp = (x + 1 == nx) ? 0 : x + 1, xm = (x == 0) ? nx - 1 : x - 1;
+    if (BC == 2) {   // open sides: psi beyond the lattice is that of the edge column
+        xp = (x + 1 == nx) ? x : x + 1;
+        xm = (x == 0) ? 0 : x - 1;
+    }
     int yp, ym;
-    if (WALLS) {
+    if (BC != 0) {
         yp = (y + 1 == ny) ? y : y + 1;
         ym = (y == 0) ? 0 : y - 1;
     } else {
@@ -139,7 +159,7 @@ __device__ __forceinline__ void site_macro(const T *__restrict__ g, const A *__r
     vy = (jy + A(0.5) * Fy) * rinv;
 }
 
-template <typename T, bool WALLS>
+template <typename T, int BC>
 __global__ void k_macro_fields(const T *__restrict__ g, const Arith<T> *__restrict__ psi,
                                const DevConsts<Arith<T>> P, int nx, int ny, int pitch,
                                long long plane, double *__restrict__ rho,
@@ -151,12 +171,12 @@ __global__ void k_macro_fields(const T *__restrict__ g, const Arith<T> *__restri
     if (!ux && !uy) {  // density only: psi is not needed
         A v[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) v[a] = pull_val<T, WALLS>(g, a, x, y, nx, ny, pitch, plane, P);
+        for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, y, nx, ny, pitch, plane, P);
         rho[i] = double(sum9(v));
         return;
     }
     A r, vx, vy;
-    site_macro<T, WALLS>(g, psi, P, nx, ny, pitch, plane, x, y, r, vx, vy);
+    site_macro<T, BC>(g, psi, P, nx, ny, pitch, plane, x, y, r, vx, vy);
     if (rho) rho[i] = double(r);
     if (ux) ux[i] = double(vx);
     if (uy) uy[i] = double(vy);
@@ -165,7 +185,7 @@ __global__ void k_macro_fields(const T *__restrict__ g, const Arith<T> *__restri
 
 // Block b reduces the contiguous site range [b*chunk, (b+1)*chunk) in FP64 with a fixed
 // per-thread order and a fixed shared-memory tree: the result does not depend on timing.
-template <typename T, bool WALLS>
+template <typename T, int BC>
 __global__ void __launch_bounds__(RED_THREADS)
 k_macro_reduce(const T *__restrict__ g, const Arith<T> *__restrict__ psi,
                const DevConsts<Arith<T>> P, int nx, int ny, int pitch, long long plane,
@@ -178,7 +198,7 @@ k_macro_reduce(const T *__restrict__ g, const Arith<T> *__restrict__ psi,
     for (long long i = beg + threadIdx.x; i < end; i += RED_THREADS) {
         const int y = (int)(i / nx), x = (int)(i % nx);
         Arith<T> r, vx, vy;
-        site_macro<T, WALLS>(g, psi, P, nx, ny, pitch, plane, x, y, r, vx, vy);
+        site_macro<T, BC>(g, psi, P, nx, ny, pitch, plane, x, y, r, vx, vy);
         const double dr = r, dvx = vx, dvy = vy;
         m += dr;
         px += dr * dvx;
@@ -250,9 +270,9 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
     StepLaunch l;
     l.variant = variant;
     l.tx = step_variant_tx(variant);
-    const int per_sm = prec == LB_FP32   ? occupancy_f32(variant, eos_kind, g.walls != 0)
-                     : prec == LB_BF16 ? occupancy_bf16(variant, eos_kind, g.walls != 0)
-                                       : occupancy_f64(variant, eos_kind, g.walls != 0);
+    const int per_sm = prec == LB_FP32   ? occupancy_f32(variant, eos_kind, g.walls)
+                     : prec == LB_BF16 ? occupancy_bf16(variant, eos_kind, g.walls)
+                                       : occupancy_f64(variant, eos_kind, g.walls);
     l.ctas_per_sm = std::max(per_sm, 1);
     if (rows_override > 0) {
         l.rows = std::min(rows_override, g.ny);
@@ -290,11 +310,11 @@ cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, 
     k_unstream<T, W><<<nb, 256, 0, st>>>(static_cast<const T *>(f), static_cast<T *>(gbuf), g.nx, \
                                          g.ny, g.pitch, g.plane)
     if (prec == LB_FP32) {
-        if (g.walls) LB_UNS(float, true); else LB_UNS(float, false);
+        BC3(LB_UNS, float);
     } else if (prec == LB_BF16) {
-        if (g.walls) LB_UNS(__nv_bfloat16, true); else LB_UNS(__nv_bfloat16, false);
+        BC3(LB_UNS, __nv_bfloat16);
     } else {
-        if (g.walls) LB_UNS(double, true); else LB_UNS(double, false);
+        BC3(LB_UNS, double);
     }
 #undef LB_UNS
     return cudaGetLastError();
@@ -306,11 +326,11 @@ cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f, cu
     k_stream<T, W><<<nb, 256, 0, st>>>(static_cast<const T *>(gbuf), static_cast<T *>(f), g.nx, \
                                        g.ny, g.pitch, g.plane)
     if (prec == LB_FP32) {
-        if (g.walls) LB_STR(float, true); else LB_STR(float, false);
+        BC3(LB_STR, float);
     } else if (prec == LB_BF16) {
-        if (g.walls) LB_STR(__nv_bfloat16, true); else LB_STR(__nv_bfloat16, false);
+        BC3(LB_STR, __nv_bfloat16);
     } else {
-        if (g.walls) LB_STR(double, true); else LB_STR(double, false);
+        BC3(LB_STR, double);
     }
 #undef LB_STR
     return cudaGetLastError();
@@ -349,8 +369,12 @@ cudaError_t launch_psi_field(int prec, const Consts &c, const Geom &g, const voi
                                                 static_cast<Arith<T> *>(psi),                \
                                                 to_dev<Arith<T>>(c), g.nx, g.ny, g.pitch,    \
                                                 g.plane, err)
-#define LB_PSI_W(T, EOSK) \
-    do { if (g.walls) LB_PSI(T, EOSK, true); else LB_PSI(T, EOSK, false); } while (0)
+#define LB_PSI_W(T, EOSK)                                              \
+    do {                                                               \
+        if (g.walls == 2) LB_PSI(T, EOSK, 2);                          \
+        else if (g.walls == 1) LB_PSI(T, EOSK, 1);                     \
+        else LB_PSI(T, EOSK, 0);                                       \
+    } while (0)
     if (prec == LB_FP32) {
         if (c.eos_kind == LB_EOS_CS) LB_PSI_W(float, LB_EOS_CS);
         else if (c.eos_kind == LB_EOS_EXP) LB_PSI_W(float, LB_EOS_EXP);
@@ -379,11 +403,11 @@ cudaError_t launch_macro_fields(int prec, const Consts &c, const Geom &g, const 
                                              to_dev<Arith<T>>(c), g.nx, g.ny, g.pitch,        \
                                              g.plane, rho, ux, uy)
     if (prec == LB_FP32) {
-        if (g.walls) LB_MAC(float, true); else LB_MAC(float, false);
+        BC3(LB_MAC, float);
     } else if (prec == LB_BF16) {
-        if (g.walls) LB_MAC(__nv_bfloat16, true); else LB_MAC(__nv_bfloat16, false);
+        BC3(LB_MAC, __nv_bfloat16);
     } else {
-        if (g.walls) LB_MAC(double, true); else LB_MAC(double, false);
+        BC3(LB_MAC, double);
     }
 #undef LB_MAC
     return cudaGetLastError();
@@ -406,11 +430,11 @@ cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const 
                                                      to_dev<Arith<T>>(c), g.nx, g.ny, g.pitch, \
                                                      g.plane, chunk, partials)
     if (prec == LB_FP32) {
-        if (g.walls) LB_RED(float, true); else LB_RED(float, false);
+        BC3(LB_RED, float);
     } else if (prec == LB_BF16) {
-        if (g.walls) LB_RED(__nv_bfloat16, true); else LB_RED(__nv_bfloat16, false);
+        BC3(LB_RED, __nv_bfloat16);
     } else {
-        if (g.walls) LB_RED(double, true); else LB_RED(double, false);
+        BC3(LB_RED, double);
     }
 #undef LB_RED
     cudaError_t e = cudaGetLastError();

@@ -232,8 +232,9 @@ extern "C" lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]) {
     if (!ctx || !out) return LB_EINVAL;
     if (lbm::ctx_view(ctx, &v) != LB_OK) return LB_EINVAL;
     if (v.sticky != LB_OK) return v.sticky;
-    if (v.prec == LB_BF16)
-        return lbm::ctx_fail(ctx, LB_EINVAL, "lb_reduce_noalloc: LB_BF16 contexts use lb_reduce",
+    if (v.prec == LB_BF16 || v.geom.walls == LB_BC_OPEN)
+        return lbm::ctx_fail(ctx, LB_EINVAL,
+                             "lb_reduce_noalloc: LB_BF16 and LB_BC_OPEN contexts use lb_reduce",
                              false);
     const long long n = (long long)v.geom.nx * v.geom.ny;
     if (n > NA_MAX_SITES) {

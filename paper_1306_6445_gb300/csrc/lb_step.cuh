@@ -140,26 +140,34 @@ __device__ __forceinline__ T sum9(const T (&v)[9]) {
                            radd(radd(v[5], v[7]), radd(v[6], v[8]))));
 }
 
-// f_a(x, y) pulled from g in global memory (periodic x; periodic y or walls).
-template <typename T, bool WALLS>
+// Boundary kinds (template parameter BC, the lb_bc value): 0 periodic; 1 half-way
+// bounce-back walls below row 0 and above row ny-1, periodic in x; 2 a bounce-back wall
+// below row 0 and open boundaries above row ny-1 and beyond columns 0 and nx-1, where a
+// population entering the lattice is pulled from the nearest lattice site (zero gradient).
+
+// f_a(x, y) pulled from g in global memory.
+template <typename T, int BC>
 __device__ __forceinline__ T pull_global(const T *__restrict__ g, int a, int x, int y, int nx,
                                          int ny, int pitch, long long plane) {
     const int ex = EXv(a), ey = EYv(a);
     int sy = y - ey;
-    if (WALLS && (sy < 0 || sy >= ny)) return g[opp(a) * plane + (long long)y * pitch + x + GH];
-    if (!WALLS) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+    if ((BC != 0 && sy < 0) || (BC == 1 && sy >= ny))
+        return g[opp(a) * plane + (long long)y * pitch + x + GH];
+    if (BC == 0) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+    if (BC == 2) sy = sy >= ny ? ny - 1 : sy;
     int sx = x - ex;
-    sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+    if (BC == 2) sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
+    else sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
     return g[a * plane + (long long)sy * pitch + sx + GH];
 }
 
 // the value of f_a(x, y) (decoded from the storage type)
-template <typename T, bool WALLS>
+template <typename T, int BC>
 __device__ __forceinline__ Arith<T> pull_val(const T *__restrict__ g, int a, int x, int y,
                                              int nx, int ny, int pitch, long long plane,
                                              const DevConsts<Arith<T>> &P) {
     // a bounced-back link reads the opposite population, whose storage shift is the same
-    return pop_dec<T>(pull_global<T, WALLS>(g, a, x, y, nx, ny, pitch, plane), a, P);
+    return pop_dec<T>(pull_global<T, BC>(g, a, x, y, nx, ny, pitch, plane), a, P);
 }
 
 // ---------------------------------------------------------------- the hot kernel
@@ -223,7 +231,7 @@ __device__ __forceinline__ V2<Arith<T>> ring_pair(const T *p, int a,
 // unshifted populations come in one aligned 2-element load. A ring row holds the stored
 // populations; the value of stored plane a is decoded with the shift of population a
 // (a bounced-back link reads the opposite population, whose shift is the same).
-template <typename T, bool WALLS, int BW, bool ADJ>
+template <typename T, int BC, int BW, bool ADJ>
 __device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, int cA, int cB,
                                       bool bottom, bool top, const DevConsts<Arith<T>> &P) {
     using A = Arith<T>;
@@ -235,7 +243,7 @@ __device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, in
     f[0] = two(r.z, 0, 0);
     f[1] = two(r.z, 1, -1);
     f[3] = two(r.z, 3, 1);
-    if (WALLS && bottom) {   // links from below row 0 are wall links: bounce back
+    if (BC != 0 && bottom) {   // links from below row 0 are wall links: bounce back
         f[2] = two(r.z, 4, 0);
         f[5] = two(r.z, 7, 0);
         f[6] = two(r.z, 8, 0);
@@ -244,10 +252,14 @@ __device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, in
         f[5] = two(r.m, 5, -1);
         f[6] = two(r.m, 6, 1);
     }
-    if (WALLS && top) {
+    if (BC == 1 && top) {
         f[4] = two(r.z, 2, 0);
         f[7] = two(r.z, 5, 0);
         f[8] = two(r.z, 6, 0);
+    } else if (BC == 2 && top) {   // open top: from the top row itself (zero gradient)
+        f[4] = two(r.z, 4, 0);
+        f[7] = two(r.z, 7, 1);
+        f[8] = two(r.z, 8, -1);
     } else {
         f[4] = two(r.p, 4, 0);
         f[7] = two(r.p, 7, 1);
@@ -309,13 +321,14 @@ __device__ __forceinline__ void grid_dependents_launch() {
 // The caller has initialised the S ring mbarriers (fresh, phase 0) and waited for the
 // previous grid. Returns 0, or ERR_TIMEOUT after a bounded wait gave up (then every copy
 // still in flight has landed, or its own bounded wait gave up too).
-template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int G>
 __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ gout,
                                      const DevConsts<Arith<T>> &P, const int nx, const int ny,
                                      const int pitch, const unsigned plane, const int x0,
                                      const int w, const int yb, const int n, const int dir,
                                      unsigned char *smem_raw, bool &bad) {
     static_assert(G == 1 || G == 2, "one or two row groups");
+    constexpr bool WALLS = BC != 0;   // rows outside the lattice are not periodic images
     static_assert(S >= G + 4, "ring rows of one iteration plus one row in flight");
     static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
     constexpr int NT = TX / 2;      // threads per row group
@@ -372,7 +385,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                                   : Ring<T>{stage(j + 1), stage(j), stage(j - 1)};
         const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
         if (act) {
-            pull2<T, WALLS, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top, P);
+            pull2<T, BC, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top, P);
             const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
             if (both) {
                 store_pair<A>(ps + c0 + 2, psi, true);
@@ -382,7 +395,12 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
         }
         if (t == NT - 1) {   // the two halo columns x0-1 and x0+w as one packed pair
             V2<A> h[9];
-            pull2<T, WALLS, BW, false>(h, r, 3, w + 4, bottom, top, P);
+            int ha = 3, hb = w + 4;
+            if (BC == 2) {   // open sides: psi beyond the lattice is that of its edge column
+                if (x0 == 0) ha = 4;
+                if (x0 + w == nx) hb = w + 3;
+            }
+            pull2<T, BC, BW, false>(h, r, ha, hb, bottom, top, P);
             const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
             ps[1] = psi.lo();
             ps[w + 2] = psi.hi();
@@ -444,15 +462,28 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             pn[6] = V2<A>(qL, q0.lo());
             pn[7] = V2<A>(mL, m0.lo());
             pn[8] = V2<A>(m0.hi(), mR);
-            collide_pair<A>(fc, pn, P);
+            collide_pair<A, BC == 2>(fc, pn, P);
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
                 store_pop_pair<T>(gout + (idx + a * plane), fc[a], both, a, P);
-            // ghost images of columns 0, 1 (right of nx-1) and nx-2, nx-1 (left of 0)
-            if (x < 2 || x + 1 >= nx - 2) {
+            if (BC == 2) {
+                // open sides: the ghost columns repeat the edge columns (zero gradient)
+                if (x == 0 || x + 1 >= nx - 1) {
+                    const unsigned rowi = (unsigned)yr * (unsigned)pitch;
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) {
+                        const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                        T *rb = gout + (rowi + a * plane);
+                        if (x == 0) rb[GH - 1] = rb[GH - 2] = v0;
+                        if (x == nx - 1) rb[nx + GH] = rb[nx + GH + 1] = v0;
+                        if (both && x + 1 == nx - 1) rb[nx + GH] = rb[nx + GH + 1] = v1;
+                    }
+                }
+            } else if (x < 2 || x + 1 >= nx - 2) {
+                // ghost images of columns 0, 1 (right of nx-1) and nx-2, nx-1 (left of 0)
                 const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
@@ -505,7 +536,7 @@ __device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
 }
 
 // Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
-template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int G>
 __global__ void __launch_bounds__(G * TX / 2)
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
@@ -527,7 +558,7 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     const int x0 = bx * TX;
     const int yb = by * rows;
     bool bad = false;
-    const int st = march<T, EOS, WALLS, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
+    const int st = march<T, EOS, BC, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
                                                min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
@@ -574,11 +605,11 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
 
 
 
-template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int G>
 cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
                          const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                          bool configure) {
-    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
+    auto kern = k_pull_collide<T, EOS, BC, TX, S, G>;
     constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
     if (configure) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -599,20 +630,26 @@ cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
                               g.pitch, (unsigned)g.plane, rows, order, err);
 }
 
+template <typename T, int EOS, int TX, int S, int G>
+cudaError_t step_bc(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
+                    void *out, int *err, cudaStream_t st, bool configure) {
+    switch (g.walls) {
+        case 0: return step_variant<T, EOS, 0, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case 1: return step_variant<T, EOS, 1, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        default:
+            // open boundaries (and nu(rho)) are compiled for FP32 and FP64 only
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) return cudaErrorInvalidValue;
+            else return step_variant<T, EOS, 2, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+    }
+}
+
 template <typename T, int TX, int S, int G>
 cudaError_t step_eos(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
                      void *out, int *err, cudaStream_t st, bool configure) {
-    const bool w = g.walls != 0;
     switch (c.eos_kind) {
-        case LB_EOS_CS:
-            return w ? step_variant<T, LB_EOS_CS, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_CS, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
-        case LB_EOS_EXP:
-            return w ? step_variant<T, LB_EOS_EXP, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_EXP, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
-        default:
-            return w ? step_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>(c, g, rows, order, tin, out, err, st, configure)
-                     : step_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case LB_EOS_CS: return step_bc<T, LB_EOS_CS, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case LB_EOS_EXP: return step_bc<T, LB_EOS_EXP, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        default: return step_bc<T, LB_EOS_PIECEWISE, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
     }
 }
 
@@ -629,11 +666,11 @@ cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l, i
     }
 }
 
-template <typename T, int EOS, bool WALLS, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int G>
 int occupancy_variant() {
     int n = 0;
     constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
-    auto kern = k_pull_collide<T, EOS, WALLS, TX, S, G>;
+    auto kern = k_pull_collide<T, EOS, BC, TX, S, G>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, G * TX / 2, smem) != cudaSuccess)
@@ -641,20 +678,28 @@ int occupancy_variant() {
     return n;
 }
 
-template <typename T, int TX, int S, int G>
-int occupancy_eos(int eos, bool w) {
-    switch (eos) {
-        case LB_EOS_CS:
-            return w ? occupancy_variant<T, LB_EOS_CS, true, TX, S, G>() : occupancy_variant<T, LB_EOS_CS, false, TX, S, G>();
-        case LB_EOS_EXP:
-            return w ? occupancy_variant<T, LB_EOS_EXP, true, TX, S, G>() : occupancy_variant<T, LB_EOS_EXP, false, TX, S, G>();
+template <typename T, int EOS, int TX, int S, int G>
+int occupancy_bc(int bc) {
+    switch (bc) {
+        case 0: return occupancy_variant<T, EOS, 0, TX, S, G>();
+        case 1: return occupancy_variant<T, EOS, 1, TX, S, G>();
         default:
-            return w ? occupancy_variant<T, LB_EOS_PIECEWISE, true, TX, S, G>() : occupancy_variant<T, LB_EOS_PIECEWISE, false, TX, S, G>();
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) return 0;
+            else return occupancy_variant<T, EOS, 2, TX, S, G>();
+    }
+}
+
+template <typename T, int TX, int S, int G>
+int occupancy_eos(int eos, int bc) {
+    switch (eos) {
+        case LB_EOS_CS: return occupancy_bc<T, LB_EOS_CS, TX, S, G>(bc);
+        case LB_EOS_EXP: return occupancy_bc<T, LB_EOS_EXP, TX, S, G>(bc);
+        default: return occupancy_bc<T, LB_EOS_PIECEWISE, TX, S, G>(bc);
     }
 }
 
 template <typename T>
-int occupancy(int variant, int eos, bool w) {
+int occupancy(int variant, int eos, int w) {
     switch (variant) {
         case 0: return occupancy_eos<T, 128, 5, 1>(eos, w);
         case 1: return occupancy_eos<T, 128, 6, 1>(eos, w);

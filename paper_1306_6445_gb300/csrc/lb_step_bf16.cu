@@ -10,8 +10,8 @@ cudaError_t step_bf16(const Consts &c, const Geom &g, const StepLaunch &l, int o
                               gout, err, st, configure);
 }
 
-int occupancy_bf16(int variant, int eos_kind, bool walls) {
-    return occupancy<__nv_bfloat16>(variant, eos_kind, walls);
+int occupancy_bf16(int variant, int eos_kind, int bc) {
+    return occupancy<__nv_bfloat16>(variant, eos_kind, bc);
 }
 
 }  // namespace lbm

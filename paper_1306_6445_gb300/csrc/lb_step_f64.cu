@@ -10,8 +10,8 @@ cudaError_t step_f64(const Consts &c, const Geom &g, const StepLaunch &l, int or
                               gout, err, st, configure);
 }
 
-int occupancy_f64(int variant, int eos_kind, bool walls) {
-    return occupancy<double>(variant, eos_kind, walls);
+int occupancy_f64(int variant, int eos_kind, int bc) {
+    return occupancy<double>(variant, eos_kind, bc);
 }
 
 }  // namespace lbm

@@ -125,3 +125,18 @@ def mlp_random_data(n: int, seed: int = DEFAULT_SEED):
                   rng.uniform(0.3, 0.6, n), np.exp(rng.uniform(np.log(1e-3), np.log(0.15), n))],
                  axis=1)
     return x.astype(np.float32), y.astype(np.float32)
+
+
+def splash_state(nx: int, ny: int, film: float, radius: float, gap: float, speed: float,
+                 rho_l: float, rho_v: float, width: float = 2.0):
+    """Droplet above a liquid film (Sec. V.C): a film of height `film` on the bottom and a
+    droplet of `radius` centred at (nx/2, film + radius + gap) moving down at `speed`;
+    tanh interfaces of the given width. Returns (rho, ux, uy) as [ny][nx] arrays."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    xc, yc = 0.5 * nx, film + radius + gap
+    f_film = 0.5 * (1.0 - np.tanh(2.0 * (y + 0.5 - film) / width))
+    f_drop = 0.5 * (1.0 - np.tanh(2.0 * (np.hypot(x - xc, y - yc) - radius) / width))
+    rho = rho_v + (rho_l - rho_v) * np.maximum(f_film, f_drop)
+    ux = np.zeros_like(rho)
+    uy = -speed * f_drop
+    return rho, ux, uy

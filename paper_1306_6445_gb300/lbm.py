@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "L
 LB_EOS_CS, LB_EOS_EXP, LB_EOS_PIECEWISE = 0, 1, 2
 LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
 PRECS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16": LB_BF16}
-LB_BC_PERIODIC, LB_BC_WALLS_Y = 0, 1
+LB_BC_PERIODIC, LB_BC_WALLS_Y, LB_BC_OPEN = 0, 1, 2
 
 # every exported symbol of include/lb.h
 EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_u", "lb_step",
@@ -32,7 +32,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
-            "lb_autotune", "lb_set_storage_shift",
+            "lb_autotune", "lb_set_storage_shift", "lb_set_viscosity_switch",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
@@ -115,6 +115,7 @@ def load_library():
         "lb_set_launch": (I, [P, I, I]),
         "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
         "lb_set_storage_shift": (I, [P, D]),
+        "lb_set_viscosity_switch": (I, [P, D, D]),
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
         "lb_reduce_noalloc": (I, [P, DP]),
@@ -336,6 +337,11 @@ def lb_autotune(ctx, trial_steps: int = 5):
     return v.value, r.value
 
 
+def lb_set_viscosity_switch(ctx, rho_1: float, s_v_vapour: float):
+    _check(load_library().lb_set_viscosity_switch(ctx, float(rho_1), float(s_v_vapour)),
+           "lb_set_viscosity_switch", ctx)
+
+
 def lb_set_storage_shift(ctx, rho_s: float):
     _check(load_library().lb_set_storage_shift(ctx, float(rho_s)), "lb_set_storage_shift", ctx)
 
@@ -388,6 +394,8 @@ class Lattice:
     walls_y: bool = False
     buffers: str = "torch"
     storage_shift: float = 0.0   # rho_s of prec="bf16" (stored BF16 of f_a - w_a rho_s)
+    open_bc: bool = False         # LB_BC_OPEN: wall below, open top and sides (Sec. V.C)
+    viscosity_switch: tuple = None   # (rho_1, s_v where rho < rho_1), LB_BC_OPEN only
 
     def __post_init__(self):
         if self.prec not in PRECS:
@@ -395,7 +403,9 @@ class Lattice:
         self._prec = PRECS[self.prec]
         # host population arrays: float64 / float32, or the raw 16-bit patterns for bf16
         self.dtype = {LB_FP64: np.float64, LB_FP32: np.float32, LB_BF16: np.uint16}[self._prec]
-        bc = LB_BC_WALLS_Y if self.walls_y else LB_BC_PERIODIC
+        if self.walls_y and self.open_bc:
+            raise LBError(LB_EINVAL, "Lattice", "walls_y and open_bc exclude each other")
+        bc = LB_BC_OPEN if self.open_bc else (LB_BC_WALLS_Y if self.walls_y else LB_BC_PERIODIC)
         self._tensors = None
         if self.buffers == "torch":
             import torch
@@ -413,6 +423,8 @@ class Lattice:
                                self.rates, self._prec, bc, None)
         if self._prec == LB_BF16:
             lb_set_storage_shift(self.ctx, self.storage_shift)
+        if self.viscosity_switch is not None:
+            lb_set_viscosity_switch(self.ctx, *self.viscosity_switch)
 
     # --- state
     def set_rho_u(self, rho, ux=None, uy=None):

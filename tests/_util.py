@@ -5,14 +5,16 @@ from oracle import eos as OE
 from oracle import lattice as OL
 
 
-def oracle_params(eos, G, kappa, sigma_force, rates, walls_y=False) -> OL.Params:
+def oracle_params(eos, G, kappa, sigma_force, rates, walls_y=False, open_bc=False,
+                  visc_switch=None) -> OL.Params:
     """Product EOSParams / RateParams -> oracle Params (same numbers, separate code)."""
     oe = OE.EOS(kind=eos.kind, a=eos.a, b=eos.b, R=eos.R, T=eos.T, psi0=eos.psi0,
                 rho0=eos.rho0, theta_v=eos.theta_v, theta_m=eos.theta_m, theta_l=eos.theta_l,
                 rho1=eos.rho1, rho2=eos.rho2)
     r = OL.Rates(s_rho=rates.s_rho, s_e=rates.s_e, s_zeta=rates.s_zeta, s_j=rates.s_j,
                  s_q=rates.s_q, s_v=rates.s_v)
-    return OL.Params(eos=oe, G=G, kappa=kappa, sigma_force=sigma_force, rates=r, walls_y=walls_y)
+    return OL.Params(eos=oe, G=G, kappa=kappa, sigma_force=sigma_force, rates=r, walls_y=walls_y,
+                     open_bc=open_bc, visc_switch=visc_switch)
 
 
 def window(f, x, y, walls_y, half=2):

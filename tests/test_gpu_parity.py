@@ -75,7 +75,7 @@ def test_steps_match_oracle_elementwise(lbm, prec, walls, kind, size):
     lat = lbm.Lattice(nx, ny, eos, G, kappa=kappa, sigma_force=sigma, rates=rates, prec=prec,
                       walls_y=walls)
     lat.set_populations(f0)
-    f0 = lat.populations().astype(np.float64)   # the values the GPU actually holds
+    f0 = f0.astype(lat.dtype).astype(np.float64)   # the values the GPU holds (storage type)
     p = oracle_params(eos, G, kappa, sigma, rates, walls)
     n = 1 if max(nx, ny) > 150 else 4
     lat.step(n)
