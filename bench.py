@@ -86,7 +86,7 @@ def measured_peaks():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("lb_device.cuh", "lb_kernels.cu"):
+    for name in ("lb_device.cuh", "lb_step.cuh", "lb_step_f32.cu"):
         with open(os.path.join(ROOT, "paper_1306_6445_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
