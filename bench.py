@@ -235,16 +235,25 @@ def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
     return el, bi, bo
 
 
-def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=6):
+def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=6, dist=None):
     """The batched Laplace-law sweep: n_lat periodic droplet lattices drawn with the given
     seed (side U{64..512 step 32}, R/side U[0.15, 0.35], T/Tc U[0.65, 0.95], kappa
     U[0, 0.95], tau_v U[0.6, 1.2]; CS a=1 b=4 R=1, G=-1, sigma_F=0.087, Maxwell initial
     densities, FP32), `steps` time steps each, in one persistent launch per step replayed
     from CUDA graphs. Compared with running `sample` of the lattices one by one through
     lb_step (extrapolated to all), and with FP64 single-lattice runs of `check` small ones
-    (surface tension error, both measured on the GPU by lb_batch_measure)."""
+    (surface tension error, both measured on the GPU by lb_batch_measure).
+
+    Under torchrun the lattices are split across ranks (independent problems, no
+    data-path communication, site counts balanced); every rank times its own batch and
+    the whole-job rate uses the slowest rank's time (weak scaling in lattices)."""
     import numpy as np
-    draws = inputs.batch_draws(n_lat, seed)
+    from paper_1306_6445_gb300 import shard
+    world = dist.get_world_size() if dist is not None else 1
+    rank = dist.get_rank() if dist is not None else 0
+    all_draws = inputs.batch_draws(n_lat, seed)
+    mine = shard.assign([d["side"] ** 2 for d in all_draws], world)[rank]
+    draws = [all_draws[i] for i in mine]
     descs, rhos = [], []
     for d in draws:
         eos = lbm.cs_eos(d["t_over_tc"])
@@ -254,23 +263,30 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
                                      rates=lbm.RateParams(s_v=1.0 / d["tau_v"])))
         rhos.append((d["radius"], rl, rv))
     radii = np.array([r[0] for r in rhos])
-    sites = sum(d.nx * d.ny for d in descs)
     b = lbm.Batch(descs, prec="fp32")
     variant, rows = b.autotune(3)
     for i, (d, (R, rl, rv)) in enumerate(zip(descs, rhos)):
         b.set_rho_u(i, inputs.droplet_density(d.nx, d.ny, R, rl, rv))
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     b.step(steps)
     b.sync()
     el = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([el], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
     meas = b.measure(radii)
+    table = shard.gather_rows(meas, mine, n_lat, dist)   # every lattice's measurement
     launch = b.launch()
     b.close()
-    failed = int(meas[:, 7].sum())
-    # the same lattices one by one (a random sample, extrapolated)
+    failed = int(table[:, 7].sum())
+    sites_all = sum(d["side"] ** 2 for d in all_draws)
+    # this rank's lattices one by one (a random sample, extrapolated)
     rng = np.random.default_rng(seed + 1)
-    pick = rng.choice(n_lat, size=min(sample, n_lat), replace=False)
+    pick = rng.choice(len(descs), size=min(sample, len(descs)), replace=False)
     t_seq = 0.0
     for i in pick:
         d = descs[i]
@@ -298,16 +314,16 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
         one.close()
         errs.append(abs(meas[i, 0] - th64) / abs(th64))
     return {
-        "lattices": n_lat, "steps": steps, "sites": sites, "failed": failed,
-        "seconds": round(el, 4),
+        "lattices": n_lat, "steps": steps, "sites": sites_all, "failed": failed,
+        "ranks": world, "seconds": round(el, 4),
         "droplets_per_s": round(n_lat / el, 2),
-        "mlups": round(sites * steps / el / 1e6, 1),
-        "sequential_droplets_per_s": round(1.0 / seq_per_lattice, 2),
-        "speedup_vs_sequential": round(seq_per_lattice * n_lat / el, 2),
+        "mlups": round(sites_all * steps / el / 1e6, 1),
+        "sequential_droplets_per_s": round(world / seq_per_lattice, 2),
+        "speedup_vs_sequential": round(seq_per_lattice * n_lat / (el * world), 2),
         "sigma_rel_err_vs_fp64_max": round(float(max(errs)), 6) if errs else None,
         "sigma_err_sample": len(errs),
         "launch": launch, "autotuned": {"variant": variant, "rows": rows},
-        "theta_median": float(np.median(meas[meas[:, 7] == 0, 0])) if failed < n_lat else None,
+        "theta_median": float(np.median(table[table[:, 7] == 0, 0])) if failed < n_lat else None,
     }
 
 
@@ -557,7 +573,8 @@ def native(args):
 
     batched = None
     if args.batch_steps > 0:
-        batched = batched_sweep(lbm, torch, inputs, args.batch_lattices, args.batch_steps)
+        batched = batched_sweep(lbm, torch, inputs, args.batch_lattices, args.batch_steps,
+                                dist=dist)
     surr = splash = None
     if not args.no_surrogate:
         net, surr = surrogate_leg(lbm, torch)
