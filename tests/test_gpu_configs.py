@@ -1,0 +1,101 @@
+"""The large lattice workloads at their full sizes on the GPU.
+
+- 2048 x 2048 droplet, FP32 against FP64 over 20000 steps (CS 0.8 T_c, R = 200): density
+  ratio and the Laplace reading within 0.5 %. This compares one trajectory in two
+  precisions: at 20000 steps the 2048^2 box still rings acoustically, so the Laplace
+  reading is not yet the surface tension (it is even negative).
+- 4096 x 2048 capillary wave with walls in y (layer height 1024, wavelength 4096/k,
+  amplitude 0.01 wavelength), FP32, 50000 steps. At this scale the period (about 1.1e5
+  steps at k = 4, and longer at k = 1, 2) exceeds the run, so the frequency is fitted to
+  the interface height over the part of a period the run covers, and compared with the
+  finite-depth dispersion relation (Eq. 24 read with omega^2) using the flat-interface
+  surface tension of Eq. 22."""
+import numpy as np
+import pytest
+
+from oracle import diagnostics as D
+from oracle import eos as OE
+from paper_1306_6445_gb300 import inputs as I
+
+from _util import oracle_params
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+scipy_optimize = pytest.importorskip("scipy.optimize")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_6445_gb300 import _build
+
+    _build.build()
+    from paper_1306_6445_gb300 import lbm as mod
+
+    mod.load_library()
+    return mod
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
+def test_2048_droplet_fp32_matches_fp64_after_20000_steps(lbm, kappa):
+    eos = lbm.cs_eos(0.8)
+    rates = lbm.RateParams.from_viscosity(0.1)
+    pv, pl, _ = OE.mechanical_stability(OE.EOS(kind="cs", T=eos.T), -1.0, 0.0)
+    rho0 = I.droplet_density(2048, 2048, 200.0, pl, pv)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        lat = lbm.Lattice(2048, 2048, eos, -1.0, kappa=kappa, rates=rates, prec=prec)
+        lat.set_rho_u(rho0)
+        lat.autotune(2)
+        lat.step(20000)
+        r = lat.rho()
+        lat.close()
+        res[prec] = D.laplace(r, oracle_params(eos, -1.0, kappa, 0.0, rates))
+    a, b = res["fp64"], res["fp32"]
+    print(f"kappa {kappa}: ratio fp64 {a['rho_in'] / a['rho_out']:.5f} "
+          f"fp32 {b['rho_in'] / b['rho_out']:.5f}; theta fp64 {a['theta']:.6g} "
+          f"fp32 {b['theta']:.6g}")
+    assert b["rho_in"] / b["rho_out"] == pytest.approx(a["rho_in"] / a["rho_out"], rel=5e-3)
+    assert b["theta"] == pytest.approx(a["theta"], rel=5e-3)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.5])
+def test_4096x2048_capillary_wave_frequency_follows_the_dispersion_relation(lbm, kappa):
+    nx, ny, h, k = 4096, 2048, 1024.0, 4
+    lam = nx / k
+    nu = 0.1     # the CS vapour (rho_v = 0.008) leaves the EOS branch at nu = 0.02
+    eos = lbm.cs_eos(0.8)
+    oeos = OE.EOS(kind="cs", T=eos.T)
+    pv, pl, _ = OE.mechanical_stability(oeos, -1.0, 0.0)
+    theta = OE.flat_surface_tension(oeos, -1.0, kappa)
+    kk = 2 * np.pi / lam
+    omega0 = np.sqrt(theta * kk ** 3 / (pl / np.tanh(kk * h) + pv / np.tanh(kk * (ny - h))))
+    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=kappa, rates=lbm.RateParams.from_viscosity(nu),
+                      prec="fp32", walls_y=True)
+    lat.set_rho_u(I.layer_density(nx, ny, h, pl, pv, width=2.0, amplitude=0.01 * lam,
+                                  wavenumber=k))
+    lat.autotune(2)
+    ts, hs = [], []
+    mid = 0.5 * (pl + pv)
+    while lat.steps_done <= 50000:
+        rho = lat.rho()
+        hs.append(D.interface_height(rho[:, 0], mid) - h)        # a crest column
+        ts.append(lat.steps_done)
+        lat.step(1000)
+    lat.close()
+    ts, hs = np.array(ts, float), np.array(hs)
+
+    # the crest height oscillates about the undisturbed level (mass conservation keeps the
+    # mean layer height): a damped cosine without an offset
+    def model(t, a, w, g):
+        return a * np.exp(-g * t) * np.cos(w * t)
+
+    p, _ = scipy_optimize.curve_fit(model, ts, hs, p0=(hs[0], omega0, 1e-6), maxfev=20000)
+    a, w, g = p
+    print("crest height every 5000 steps:", np.round(hs[::5], 3))
+    print(f"kappa {kappa}: omega fitted {w:.5g}, dispersion {omega0:.5g} "
+          f"({w / omega0 - 1:+.2%}), amplitude {a:.3g} (set {0.01 * lam:.3g}), damping {g:.3g}")
+    assert abs(hs[0] - 0.01 * lam) < 1.0
+    assert w == pytest.approx(omega0, rel=0.05)
