@@ -48,7 +48,7 @@ ALG_BYTES_PER_SITE = {"fp32": 72, "fp64": 144, "bf16": 36}   # 9 populations rea
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--nx", type=int, default=NX)
@@ -107,7 +107,9 @@ def profiled_traffic(prec: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, one line every 50 ms from a single
+    `nvidia-smi -lms 50` process that runs only while the sampler is entered (the timed
+    region)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -116,28 +118,37 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.samples = []
-        self._stop = threading.Event()
-        self._t = threading.Thread(target=self._run, daemon=True)
+        self._p = None
+        self._t = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
-                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
-                                     capture_output=True, text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([s.strip() for s in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._p.stdout:
+            parts = [x.strip() for x in line.strip().split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
 
     def __enter__(self):
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.1)               # the first line is out before the region starts
+        except Exception:
+            self._p = None
         return self
 
     def __exit__(self, *exc):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is not None:
+            time.sleep(0.06)              # one more line covering the end of the region
+            self._p.terminate()           # this object's own child process
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
         if not self.samples:
@@ -164,7 +175,8 @@ def droplet_setup(lbm, inputs, nx, ny):
 # native arm
 # --------------------------------------------------------------------------------------
 
-def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist, launch=None):
+def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist, launch=None,
+                   clocks=None):
     eos, rates, rho = droplet_setup(lbm, inputs, nx, ny)
     # BF16 storage: shift by the vapour density (most sites of the droplet lattice)
     lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, rates=rates, prec=prec,
@@ -186,6 +198,8 @@ def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist,
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.__enter__()
     t0.record(stream)
     for k in range(steps):
         ev[k][0].record(stream)
@@ -194,6 +208,8 @@ def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist,
         lat.reduce()
     t1.record(stream)
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.__exit__(None, None, None)
     if dist is not None:
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
@@ -525,10 +541,10 @@ def native(args):
 
     nx, ny, inner, K, W = args.nx, args.ny, args.inner, args.steps, args.warmup
     sites = nx * ny
-    with ClockSampler(local) as clocks:
-        total_ms, kern_ms, launches, shape = time_precision(lbm, torch, inputs, "fp32", nx, ny,
-                                                            inner, K, W, dist,
-                                                            (args.variant, args.rows))
+    clocks = ClockSampler(local)
+    total_ms, kern_ms, launches, shape = time_precision(lbm, torch, inputs, "fp32", nx, ny,
+                                                        inner, K, W, dist,
+                                                        (args.variant, args.rows), clocks)
     t = torch.tensor([total_ms], device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
