@@ -84,26 +84,32 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(prec: str = "fp32") -> str:
     h = hashlib.sha256()
-    for name in ("lb_device.cuh", "lb_step.cuh", "lb_step_f32.cu"):
+    unit = {"fp32": "lb_step_f32.cu", "fp64": "lb_step_f64.cu", "bf16": "lb_step_bf16.cu"}[prec]
+    for name in ("lb_device.cuh", "lb_step.cuh", unit):
         with open(os.path.join(ROOT, "paper_1306_6445_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(prec: str):
-    """DRAM bytes per fused-step launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"fused_step_{prec}_2048sq.md")
+def profiled_value(name: str, key: str, prec: str):
+    """A figure of a committed ncu summary (profiles/<name>.md, `key: value`), if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not (m_sha and m_b) or m_sha.group(1) != kernel_source_sha():
+    m_v = re.search(rf"{key}:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_v) or m_sha.group(1) != kernel_source_sha(prec):
         return None
-    return float(m_b.group(1))
+    return float(m_v.group(1))
+
+
+def profiled_traffic(prec: str):
+    """DRAM bytes per fused-step launch of the 2048^2 workload from the committed ncu summary."""
+    return profiled_value(f"fused_step_{prec}_2048sq", "dram_bytes_per_launch", prec)
 
 
 class ClockSampler:
@@ -217,6 +223,22 @@ def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist,
     launches = steps * (inner * lbm.lb_kernels_per_step(lat.ctx) + 3)
     lat.close()
     return total_ms, step_kernel_ms / (steps * inner), launches, shape
+
+
+def fp64_alu_roofline(lbm, torch, sites, kern_ms):
+    """The FP64 update against its ALU roof: FP64-pipe thread instructions per site (ncu
+    count, committed summary) x sites / the step kernel's CUDA-event time, against the FP64
+    FMA rate the library's probe measures on this GPU now (every FP64 add, multiply and FMA
+    takes one issue slot of the same pipe)."""
+    peak = lbm.lb_probe_fp64_fma_rate(torch.cuda.current_stream().cuda_stream, 4096)
+    inst = profiled_value("fused_step_fp64_2048sq", "fp64_pipe_inst_per_site", "fp64")
+    out = {"bound": "alu", "peak": round(peak / 1e9, 2), "unit": "G FP64 inst/s",
+           "peak_source": "lb_probe_fp64_fma_rate (measured FP64 FMA rate)",
+           "inst_per_site": inst, "achieved": None, "frac": None}
+    if inst is not None:
+        achieved = inst * sites / (kern_ms * 1e-3)
+        out.update(achieved=round(achieved / 1e9, 2), frac=round(achieved / peak, 4))
+    return out
 
 
 def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
@@ -568,7 +590,7 @@ def native(args):
     fp64 = {"value": round(sites * inner * fk / (f_total * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "kernel_ms": round(f_kern, 5),
             "hbm_frac": round(alg64 / (f_kern * 1e-3) / 1e9 / hbm, 4), "launch": shape64,
-            "note": "FP64 update is bound by FP64 ALU throughput on GB300, not HBM"}
+            "roofline": fp64_alu_roofline(lbm, torch, sites, f_kern)}
 
     # BF16 storage leg: speed, and the error table of a converged droplet against FP64
     bf16 = None

@@ -305,6 +305,19 @@ const char *lb_batch_last_error(const lb_batch *b);
 void lb_batch_free(lb_batch *b);
 
 /* ---------------------------------------------------------------------------------
+ * Measurement (no counterpart in the paper).
+ * --------------------------------------------------------------------------------- */
+
+/* FP64 fused multiply-add throughput of the current device, the ALU roof of the LB_FP64
+ * update: 8 blocks of 256 threads per SM, each thread running 8 independent chains of
+ * `iters` FP64 FMAs, timed with CUDA events on `cuda_stream` (a cudaStream_t, or NULL for
+ * the legacy default stream) after one untimed launch. *fma_per_s receives FP64 FMA
+ * thread instructions per second (one FMA = 2 flops). iters = 4096 runs about 15 ms on a
+ * GPU with GB300's FP64 rate. Synchronises the stream.
+ * Errors: LB_EINVAL for iters < 1 or a NULL output, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_probe_fp64_fma_rate(void *cuda_stream, int iters, double *fma_per_s);
+
+/* ---------------------------------------------------------------------------------
  * Host-side thermodynamic set-up helpers (no GPU work). They give the Carnahan-
  * Starling critical point and the Maxwell coexistence densities used to build
  * initial droplets (Sec. II; the Maxwell rule is equal area in 1/rho).

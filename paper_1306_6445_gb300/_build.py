@@ -22,7 +22,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblb_gb300.so")
 SOURCES = ["lb_step_f32.cu", "lb_step_f64.cu", "lb_step_bf16.cu", "lb_batch_kernels.cu",
            "lb_kernels.cu", "lb_api.cu", "lb_thermo.cpp", "lb_noalloc.cu", "lb_batch.cu",
-           "lb_mlp.cu"]
+           "lb_mlp.cu", "lb_probe.cu"]
 HEADERS = ["lb_internal.h", "lb_device.cuh", "lb_step.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",

@@ -31,6 +31,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
+            "lb_probe_fp64_fma_rate",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
             "lb_autotune", "lb_set_storage_shift", "lb_set_viscosity_switch",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
@@ -111,6 +112,7 @@ def load_library():
         "lb_free": (None, [P]),
         "lb_cs_critical": (I, [D, D, D, DP, DP]),
         "lb_maxwell": (I, [C.POINTER(c_lb_eos), D, DP, DP, DP]),
+        "lb_probe_fp64_fma_rate": (I, [P, I, DP]),
         "lb_launch_variants": (I, []),
         "lb_set_launch": (I, [P, I, I]),
         "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
@@ -233,6 +235,15 @@ def lb_maxwell(eos: EOSParams, G: float):
     _check(load_library().lb_maxwell(C.byref(e), G, C.byref(rv), C.byref(rl), C.byref(pb)),
            "lb_maxwell")
     return rv.value, rl.value, pb.value
+
+
+def lb_probe_fp64_fma_rate(stream=None, iters: int = 4096) -> float:
+    """FP64 FMA thread instructions per second of the current device (the ALU roof of the
+    FP64 update); `stream` a cudaStream_t handle (int) or None for the default stream."""
+    r = C.c_double()
+    _check(load_library().lb_probe_fp64_fma_rate(C.c_void_p(stream or 0), iters, C.byref(r)),
+           "lb_probe_fp64_fma_rate")
+    return r.value
 
 
 def lb_pitch(nx: int, prec: int) -> int:
