@@ -388,12 +388,18 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
                                         c->stream);
             };
             e = once();
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = once();
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            // best of three timed runs: a single short run is at the mercy of clock and
+            // memory-controller noise of a few percent, the size of the differences sought
             float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, c->stream);
+                for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = once();
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e == cudaSuccess && (rep == 0 || t < ms)) ms = t;
+            }
             if (e != cudaSuccess) break;
             if (best_ms == 0.f || ms < best_ms) {
                 best_ms = ms;
