@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--batch-lattices", type=int, default=512)
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-splash", action="store_true", help="skip the splash leg")
-    ap.add_argument("--splash-steps", type=int, default=40000)
+    ap.add_argument("--splash-steps", type=int, default=14000,
+                    help="splash time steps (14000 = t* 1.75, the end of the paper's run)")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate leg (converged sweep, training, judged kappa)")
     return ap.parse_args()

@@ -215,6 +215,28 @@ lb_status lb_reduce(lb_ctx *ctx, double out[4]);
  * LB_EINVAL for an LB_BF16 context (use lb_reduce). */
 lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]);
 
+/* Laplace-law measurement of a droplet centred at ((nx-1)/2, (ny-1)/2) (Sec. V.A), on the
+ * GPU from the current state: FP64 sums over all sites in a fixed order (the same bits on
+ * every call), with the definitions of lb_batch_measure. radius: nominal droplet radius,
+ * used only for the masks (inside r < radius/2, outside r > radius + 0.3 min(nx, ny)/2).
+ * out[0] = theta = (p_in - p_out) R, 1 = rho_in, 2 = rho_out (mask means), 3 = R from the
+ * mass, sqrt((M - rho_out N) / (pi (rho_in - rho_out))), 4 = p_in, 5 = p_out (means of
+ * p = rho/3 + G psi^2/2, the bulk part of Eq. 20), 6 = M = total mass, 7 = 1 if a site has
+ * a non-finite density or pressure or psi off its real branch (else 0). The context is
+ * not poisoned by a failed measurement. Synchronises.
+ * Errors: LB_EINVAL for a NULL out or a radius that is not positive and finite, LB_ENOMEM,
+ * LB_ECUDA, and the sticky errors of lb_sync. */
+lb_status lb_measure_droplet(lb_ctx *ctx, double radius, double out[8]);
+
+/* Height of the liquid-vapour interface in every column (Sec. V.B capillary wave), on
+ * the GPU from the current state: heights[x] = (y - 1) + (rho(x, y-1) - rho_mid) /
+ * (rho(x, y-1) - rho(x, y)) with y the lowest row whose density is below rho_mid (liquid
+ * below the interface), the densities those of lb_get_rho; NaN where row 0 is already
+ * below rho_mid or no row is. heights: caller-owned host buffer of nx doubles.
+ * Synchronises. Errors: LB_EINVAL for a NULL buffer or a non-finite rho_mid, LB_ENOMEM,
+ * LB_ECUDA, and the sticky errors of lb_sync. */
+lb_status lb_interface_height(lb_ctx *ctx, double rho_mid, double *heights);
+
 /* Number of time steps taken since lb_set_rho_u. */
 long long lb_steps_done(const lb_ctx *ctx);
 

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -28,8 +29,9 @@ struct lb_ctx {
     int num_sms = 0;
     int *d_err = nullptr;        // device error bits
     double *d_field = nullptr;   // diagnostics: two nx*ny double fields
-    double *d_partials = nullptr;
-    double *d_out4 = nullptr;
+    double *d_partials = nullptr;  // 8 doubles per reduction block
+    double *d_out8 = nullptr;      // 8 doubles
+    int *d_first = nullptr;        // interface height: nx ints
     double *d_host_in = nullptr; // 3*nx*ny staging for lb_set_rho_u
     lbm::StepLaunch launch{};
     long long steps = 0;
@@ -226,8 +228,9 @@ lb_status ensure_diag(lb_ctx *c) {
     const size_t n = (size_t)c->geom.nx * c->geom.ny;
     if (!c->d_field) LB_CUDA(c, cudaMalloc(&c->d_field, 2 * n * sizeof(double)));
     if (!c->d_partials)
-        LB_CUDA(c, cudaMalloc(&c->d_partials, 4 * sizeof(double) * lbm::reduce_blocks((long long)n)));
-    if (!c->d_out4) LB_CUDA(c, cudaMalloc(&c->d_out4, 4 * sizeof(double)));
+        LB_CUDA(c, cudaMalloc(&c->d_partials, 8 * sizeof(double) * lbm::reduce_blocks((long long)n)));
+    if (!c->d_out8) LB_CUDA(c, cudaMalloc(&c->d_out8, 8 * sizeof(double)));
+    if (!c->d_first) LB_CUDA(c, cudaMalloc(&c->d_first, sizeof(int) * (size_t)c->geom.nx));
     return LB_OK;
 }
 
@@ -558,13 +561,45 @@ lb_status lb_reduce(lb_ctx *c, double out[4]) {
     LB_CUDA(c, lbm::launch_psi_field(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
                                      c->d_err, c->stream));
     LB_CUDA(c, lbm::launch_macro_reduce(c->prec, c->consts, c->geom, c->f[c->cur], spare(c),
-                                        c->d_partials, c->d_out4, c->stream));
-    LB_CUDA(c, cudaMemcpyAsync(out, c->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                                        c->d_partials, c->d_out8, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(out, c->d_out8, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if ((s = sync_and_check(c)) != LB_OK) return s;
     for (int i = 0; i < 4; ++i)
         if (!std::isfinite(out[i]))
             return poison(c, LB_ENONFINITE, "lb_reduce: non-finite mass, momentum or |v|");
     return LB_OK;
+}
+
+lb_status lb_measure_droplet(lb_ctx *c, double radius, double out[8]) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!out) return fail(c, LB_EINVAL, "lb_measure_droplet: NULL");
+    if (!(radius > 0 && std::isfinite(radius)))
+        return fail(c, LB_EINVAL, "lb_measure_droplet: radius must be positive and finite");
+    if ((s = ensure_diag(c)) != LB_OK) return s;
+    const int nx = c->geom.nx, ny = c->geom.ny;
+    const double r_out = radius + 0.3 * 0.5 * std::min(nx, ny);
+    LB_CUDA(c, lbm::launch_droplet_sums(c->prec, c->consts, c->geom, c->f[c->cur],
+                                        0.5 * (nx - 1), 0.5 * (ny - 1), 0.5 * radius, r_out,
+                                        c->d_partials, c->d_out8, c->stream));
+    double m[8];
+    LB_CUDA(c, cudaMemcpyAsync(m, c->d_out8, sizeof(m), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = sync_and_check(c)) != LB_OK) return s;
+    lbm::droplet_results(m, (double)nx * ny, false, out);
+    return LB_OK;
+}
+
+lb_status lb_interface_height(lb_ctx *c, double rho_mid, double *heights) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (!heights) return fail(c, LB_EINVAL, "lb_interface_height: NULL");
+    if (!std::isfinite(rho_mid)) return fail(c, LB_EINVAL, "lb_interface_height: non-finite rho_mid");
+    if ((s = ensure_diag(c)) != LB_OK) return s;
+    LB_CUDA(c, lbm::launch_interface_height(c->prec, c->consts, c->geom, c->f[c->cur], rho_mid,
+                                            c->d_first, c->d_field, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(heights, c->d_field, sizeof(double) * (size_t)c->geom.nx,
+                               cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
 }
 
 long long lb_steps_done(const lb_ctx *c) { return c ? c->steps : 0; }
@@ -586,7 +621,8 @@ void lb_free(lb_ctx *c) {
     cudaFree(c->d_err);
     cudaFree(c->d_field);
     cudaFree(c->d_partials);
-    cudaFree(c->d_out4);
+    cudaFree(c->d_out8);
+    cudaFree(c->d_first);
     cudaFree(c->d_host_in);
     delete c;
 }

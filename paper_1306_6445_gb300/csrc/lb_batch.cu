@@ -508,26 +508,9 @@ lb_status lb_batch_measure(lb_batch *b, const double *radius, double *out) {
     if (s != LB_OK) return s;
     std::vector<int> errs(b->n);
     LB_BCUDA(b, cudaMemcpy(errs.data(), b->d_errs, b->n * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < b->n; ++i) {
-        const double *m = &raw[8 * (size_t)i];
-        const double nsites = (double)b->geom[i].nx * b->geom[i].ny;
-        const double rho_in = m[2] > 0 ? m[1] / m[2] : NAN;
-        const double rho_out = m[4] > 0 ? m[3] / m[4] : NAN;
-        const double p_in = m[2] > 0 ? m[5] / m[2] : NAN;
-        const double p_out = m[4] > 0 ? m[6] / m[4] : NAN;
-        // droplet radius from the mass, Laplace law theta = (p_in - p_out) R
-        const double R = std::sqrt((m[0] - rho_out * nsites) / (3.14159265358979323846 * (rho_in - rho_out)));
-        double *o = out + 8 * (size_t)i;
-        o[0] = (p_in - p_out) * R;
-        o[1] = rho_in;
-        o[2] = rho_out;
-        o[3] = R;
-        o[4] = p_in;
-        o[5] = p_out;
-        o[6] = m[0];
-        const bool bad = (m[7] > 0) || !std::isfinite(o[0]) || (errs[i] != 0);
-        o[7] = bad ? 1.0 : 0.0;
-    }
+    for (int i = 0; i < b->n; ++i)
+        lbm::droplet_results(&raw[8 * (size_t)i], (double)b->geom[i].nx * b->geom[i].ny,
+                             errs[i] != 0, out + 8 * (size_t)i);
     return LB_OK;
 }
 

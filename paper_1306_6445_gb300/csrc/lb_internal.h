@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "lb.h"
 
 namespace lbm {
@@ -108,6 +110,35 @@ int reduce_blocks(long long n_sites);
 cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const void *gbuf,
                                 const void *psi, double *partials, double *out4,
                                 cudaStream_t stream);
+
+// Laplace sums of a droplet (8 doubles into out8, layout of k_droplet_sums); partials must
+// hold 8 * reduce_blocks(n) doubles
+cudaError_t launch_droplet_sums(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                double cx, double cy, double r_in, double r_out,
+                                double *partials, double *out8, cudaStream_t stream);
+// interface height of every column into h (nx doubles); first: nx ints of scratch
+cudaError_t launch_interface_height(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                    double rho_mid, int *first, double *h, cudaStream_t stream);
+
+// Laplace-law results from the 8 sums of a droplet measurement (the layout of
+// lb_batch_measure / lb_measure_droplet's out): theta, rho_in, rho_out, R (from the mass),
+// p_in, p_out, mass, failed
+inline void droplet_results(const double m[8], double n_sites, bool failed, double o[8]) {
+    const double rho_in = m[2] > 0 ? m[1] / m[2] : NAN;
+    const double rho_out = m[4] > 0 ? m[3] / m[4] : NAN;
+    const double p_in = m[2] > 0 ? m[5] / m[2] : NAN;
+    const double p_out = m[4] > 0 ? m[6] / m[4] : NAN;
+    const double R = std::sqrt((m[0] - rho_out * n_sites) /
+                               (3.14159265358979323846 * (rho_in - rho_out)));
+    o[0] = (p_in - p_out) * R;
+    o[1] = rho_in;
+    o[2] = rho_out;
+    o[3] = R;
+    o[4] = p_in;
+    o[5] = p_out;
+    o[6] = m[0];
+    o[7] = (failed || m[7] > 0 || !std::isfinite(o[0])) ? 1.0 : 0.0;
+}
 
 // ---- batched step (lb_kernels.cu) --------------------------------------------------------
 // maps: 2 CUtensorMap per lattice (buffer 0, buffer 1); lats: BatchLattice<T> table

@@ -225,6 +225,118 @@ k_macro_reduce(const T *__restrict__ g, const Arith<T> *__restrict__ psi,
     if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
 }
 
+// Laplace-law sums of a droplet (Sec. V.A): block b sums the site range [b*chunk,
+// (b+1)*chunk) with a fixed per-thread order and a fixed tree. q[0] mass, q[1] / q[2] sum
+// of rho / count over r < r_in, q[3] / q[4] over r > r_out, q[5] / q[6] sum of the bulk
+// pressure p = rho/3 + (G/2) psi^2 inside / outside, q[7] sites with a non-finite rho or p
+// or psi off its real branch; r is the distance from (cx, cy).
+template <typename T, int EOS, int BC>
+__global__ void __launch_bounds__(RED_THREADS)
+k_droplet_sums(const T *__restrict__ g, const DevConsts<Arith<T>> P, int nx, int ny, int pitch,
+               long long plane, long long chunk, double cx, double cy, double r_in,
+               double r_out, double *__restrict__ partials) {
+    using A = Arith<T>;
+    __shared__ double s[8][RED_THREADS];
+    const long long n = (long long)nx * ny;
+    const long long beg = (long long)blockIdx.x * chunk;
+    const long long end = min(n, beg + chunk);
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = beg + threadIdx.x; i < end; i += RED_THREADS) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        A v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, y, nx, ny, pitch, plane, P);
+        const A rho = sum9(v);
+        bool bad = false;
+        const A psi = eos_psi<A, EOS>(rho, P, bad);
+        const double dr = double(rho);
+        const double pr = dr / 3.0 + 0.5 * double(P.G) * double(psi) * double(psi);
+        q[0] += dr;
+        const double r = sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy));
+        if (r < r_in) { q[1] += dr; q[2] += 1; q[5] += pr; }
+        if (r > r_out) { q[3] += dr; q[4] += 1; q[6] += pr; }
+        if (bad || !(dr == dr) || !(pr == pr)) q[7] += 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = q[k];
+    __syncthreads();
+    for (int wdt = RED_THREADS / 2; wdt > 0; wdt >>= 1) {
+        if (threadIdx.x < wdt) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + wdt];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Sum of nblocks partial 8-vectors in a fixed order.
+__global__ void __launch_bounds__(RED_THREADS)
+k_sum8_final(const double *__restrict__ partials, int nblocks, double *__restrict__ out) {
+    __shared__ double s[8][RED_THREADS];
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += RED_THREADS) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] += partials[b * 8 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = q[k];
+    __syncthreads();
+    for (int wdt = RED_THREADS / 2; wdt > 0; wdt >>= 1) {
+        if (threadIdx.x < wdt) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + wdt];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Interface height per column (Sec. V.B), pass 1: thread (x, segment) scans the rows of
+// its segment upward and records the first row whose density is below rho_mid in
+// first[x] (atomicMin: the minimum does not depend on the order of the updates).
+template <typename T, int BC>
+__global__ void k_interface_first(const T *__restrict__ g, const DevConsts<Arith<T>> P, int nx,
+                                  int ny, int pitch, long long plane, double rho_mid, int seg,
+                                  int *__restrict__ first) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    const int y0 = blockIdx.y * seg, y1 = min(ny, y0 + seg);
+    for (int y = y0; y < y1; ++y) {
+        Arith<T> v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, y, nx, ny, pitch, plane, P);
+        if (double(sum9(v)) < rho_mid) {
+            atomicMin(&first[x], y);
+            return;
+        }
+    }
+}
+
+// pass 2: linear interpolation between the last liquid row y-1 and the first vapour row y,
+// (y - 1) + (rho(y-1) - rho_mid) / (rho(y-1) - rho(y)); NaN where row 0 is already below
+// rho_mid or no row is
+template <typename T, int BC>
+__global__ void k_interface_height(const T *__restrict__ g, const DevConsts<Arith<T>> P, int nx,
+                                   int ny, int pitch, long long plane, double rho_mid,
+                                   const int *__restrict__ first, double *__restrict__ h) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    const int y = first[x];
+    if (y <= 0 || y >= ny) {
+        h[x] = __longlong_as_double(0x7ff8000000000000ll);   // quiet NaN
+        return;
+    }
+    auto rho_at = [&](int yy) {
+        Arith<T> v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = pull_val<T, BC>(g, a, x, yy, nx, ny, pitch, plane, P);
+        return double(sum9(v));
+    };
+    const double r0 = rho_at(y - 1), r1 = rho_at(y);
+    h[x] = double(y - 1) + (r0 - rho_mid) / (r0 - r1);
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
 k_reduce_final(const double *__restrict__ partials, int nblocks, double *__restrict__ out) {
     __shared__ double s[4][RED_THREADS];
@@ -440,6 +552,69 @@ cudaError_t launch_macro_reduce(int prec, const Consts &c, const Geom &g, const 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, RED_THREADS, 0, st>>>(partials, nb, out4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_droplet_sums(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                double cx, double cy, double r_in, double r_out,
+                                double *partials, double *out8, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    const int nb = reduce_blocks(n);
+    const long long chunk = (n + nb - 1) / nb;
+#define LB_DS(T, EOSK, W)                                                                     \
+    k_droplet_sums<T, EOSK, W><<<nb, RED_THREADS, 0, st>>>(static_cast<const T *>(gbuf),       \
+                                                           to_dev<Arith<T>>(c), g.nx, g.ny,    \
+                                                           g.pitch, g.plane, chunk, cx, cy,    \
+                                                           r_in, r_out, partials)
+#define LB_DS_W(T, EOSK)                                              \
+    do {                                                              \
+        if (g.walls == 2) LB_DS(T, EOSK, 2);                          \
+        else if (g.walls == 1) LB_DS(T, EOSK, 1);                     \
+        else LB_DS(T, EOSK, 0);                                       \
+    } while (0)
+#define LB_DS_E(T)                                                    \
+    do {                                                              \
+        if (c.eos_kind == LB_EOS_CS) LB_DS_W(T, LB_EOS_CS);           \
+        else if (c.eos_kind == LB_EOS_EXP) LB_DS_W(T, LB_EOS_EXP);    \
+        else LB_DS_W(T, LB_EOS_PIECEWISE);                            \
+    } while (0)
+    if (prec == LB_FP32) LB_DS_E(float);
+    else if (prec == LB_BF16) LB_DS_E(__nv_bfloat16);
+    else LB_DS_E(double);
+#undef LB_DS_E
+#undef LB_DS_W
+#undef LB_DS
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum8_final<<<1, RED_THREADS, 0, st>>>(partials, nb, out8);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interface_height(int prec, const Consts &c, const Geom &g, const void *gbuf,
+                                    double rho_mid, int *first, double *h, cudaStream_t st) {
+    constexpr int SEG = 64, TPB = 128;
+    // 0x7f7f7f7f: larger than any row index ("no vapour row")
+    cudaError_t e = cudaMemsetAsync(first, 0x7f, sizeof(int) * (size_t)g.nx, st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid1((g.nx + TPB - 1) / TPB, (g.ny + SEG - 1) / SEG);
+    const unsigned grid2 = (g.nx + TPB - 1) / TPB;
+#define LB_IH(T, W)                                                                           \
+    do {                                                                                      \
+        k_interface_first<T, W><<<grid1, TPB, 0, st>>>(static_cast<const T *>(gbuf),          \
+                                                       to_dev<Arith<T>>(c), g.nx, g.ny,       \
+                                                       g.pitch, g.plane, rho_mid, SEG, first); \
+        k_interface_height<T, W><<<grid2, TPB, 0, st>>>(static_cast<const T *>(gbuf),         \
+                                                        to_dev<Arith<T>>(c), g.nx, g.ny,      \
+                                                        g.pitch, g.plane, rho_mid, first, h); \
+    } while (0)
+    if (prec == LB_FP32) {
+        BC3(LB_IH, float);
+    } else if (prec == LB_BF16) {
+        BC3(LB_IH, __nv_bfloat16);
+    } else {
+        BC3(LB_IH, double);
+    }
+#undef LB_IH
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_sync", "lb_get_rho", "lb_get_u", "lb_get_populations", "lb_set_populations",
             "lb_reduce", "lb_steps_done", "lb_kernels_per_step", "lb_last_error",
             "lb_status_of", "lb_free", "lb_cs_critical", "lb_maxwell", "lb_launch_variants",
-            "lb_probe_fp64_fma_rate",
+            "lb_probe_fp64_fma_rate", "lb_measure_droplet", "lb_interface_height",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
             "lb_autotune", "lb_set_storage_shift", "lb_set_viscosity_switch",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
@@ -113,6 +113,8 @@ def load_library():
         "lb_cs_critical": (I, [D, D, D, DP, DP]),
         "lb_maxwell": (I, [C.POINTER(c_lb_eos), D, DP, DP, DP]),
         "lb_probe_fp64_fma_rate": (I, [P, I, DP]),
+        "lb_measure_droplet": (I, [P, D, DP]),
+        "lb_interface_height": (I, [P, D, DP]),
         "lb_launch_variants": (I, []),
         "lb_set_launch": (I, [P, I, I]),
         "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
@@ -318,6 +320,24 @@ def lb_reduce(ctx):
     return out
 
 
+def lb_measure_droplet(ctx, radius: float):
+    """Laplace-law measurement on the GPU (see include/lb.h): a dict with theta, rho_in,
+    rho_out, R, p_in, p_out, mass, failed."""
+    out = np.zeros(8)
+    _check(load_library().lb_measure_droplet(ctx, float(radius), _dp(out)), "lb_measure_droplet",
+           ctx)
+    keys = ("theta", "rho_in", "rho_out", "R", "p_in", "p_out", "mass", "failed")
+    return dict(zip(keys, out.tolist()))
+
+
+def lb_interface_height(ctx, rho_mid: float, nx: int):
+    """Interface height of every column (nx doubles, NaN where there is none)."""
+    out = np.zeros(nx)
+    _check(load_library().lb_interface_height(ctx, float(rho_mid), _dp(out)),
+           "lb_interface_height", ctx)
+    return out
+
+
 def lb_reduce_noalloc(ctx):
     """lb_reduce without device allocation (static scratch); see include/lb.h."""
     out = np.zeros(4)
@@ -471,6 +491,12 @@ class Lattice:
 
     def reduce(self) -> np.ndarray:
         return lb_reduce(self.ctx)
+
+    def measure_droplet(self, radius: float) -> dict:
+        return lb_measure_droplet(self.ctx, radius)
+
+    def interface_height(self, rho_mid: float) -> np.ndarray:
+        return lb_interface_height(self.ctx, rho_mid, self.nx)
 
     @property
     def steps_done(self) -> int:
