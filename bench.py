@@ -14,7 +14,7 @@ pinned host memory, density field out to pinned host memory, every step);
 duration against the measured HBM copy bandwidth; `fp64` = the same workload in FP64;
 `cpu_baseline` = the FP64 numpy oracle on one host core over a bounded sample;
 `batched` = the 512-droplet sweep in one persistent launch per step; `surrogate` = the
-network trained on a converged batched sweep and the kappa it picks, judged by Laplace
+network trained on a converged batched sweep and the kappa it picks, checked by Laplace
 runs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--splash-steps", type=int, default=14000,
                     help="splash time steps (14000 = t* 1.75, the end of the paper's run)")
     ap.add_argument("--no-surrogate", action="store_true",
-                    help="skip the surrogate leg (converged sweep, training, judged kappa)")
+                    help="skip the surrogate leg (converged sweep, training, checked kappa)")
     return ap.parse_args()
 
 
@@ -414,7 +414,7 @@ def surrogate_leg(lbm, torch, n_train=512):
     """The surrogate end to end: a converged batched Laplace sweep of n_train droplets
     (128^2, R = 32, 24000 steps, reading averaged over the last 2048), full-batch Adam
     training in the library's kernels, then kappa for the hardest targets (the smallest
-    sigma per temperature, kappa near 0.93) judged by a plain Laplace run, against the
+    sigma per temperature, kappa near 0.93) checked by a plain Laplace run, against the
     Eq. 22 law calibrated by a kappa = 0 run."""
     import numpy as np
     from paper_1306_6445_gb300 import surrogate, sweep
@@ -446,7 +446,7 @@ def surrogate_leg(lbm, torch, n_train=512):
         "us_per_adam_step": round(us_step, 2),
         "train_samples_per_s": round(int(ok.sum()) / (us_step * 1e-6), 0),
         "final_loss": losses[-1],
-        "judged_targets": len(g), "laplace_runs_per_target": float(res["runs"].mean()),
+        "checked_targets": len(g), "laplace_runs_per_target": float(res["runs"].mean()),
         "sigma_err_net_max": round(float(e_net.max()), 5),
         "sigma_err_law_max": round(float(e_law.max()), 5),
         "law_calibration_runs_per_target": 1,
@@ -458,7 +458,7 @@ def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, We=200.0, Re=500.0, U
     """Droplet splashing on a thin film at 4096 x 1024 (film 0.1 D, D = 400), FP32, CS at
     0.65 T_c with sigma_F = 0.087, U = 0.05; Re = U D / nu_L, nu_V = 20 nu_L switched at
     the mean phase density; the target surface tension follows from We = rho_L U^2 D /
-    sigma, and kappa comes from the surrogate network, judged by one Laplace run
+    sigma, and kappa comes from the surrogate network, checked by one Laplace run
     (128^2). Reports the kernel rate and the spread radius."""
     import numpy as np
     from paper_1306_6445_gb300 import splash, surrogate
@@ -499,7 +499,7 @@ def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, We=200.0, Re=500.0, U
     return {"workload": f"{nx}x{ny} splash, D={D:.0f}, film {film:.0f}, CS {t_over_tc}Tc, "
                         f"We={We:.0f}, Re={Re:.0f}, U={U}, FP32, {steps} steps",
             "kappa_from_surrogate": round(kappa, 5), "sigma_target": sigma_t,
-            "sigma_judged_rel_err": round(float(res["rel_err"][0]), 5),
+            "sigma_checked_rel_err": round(float(res["rel_err"][0]), 5),
             "laplace_runs": int(res["runs"][0]),
             "mlups": round(nx * ny * done / (ms * 1e-3) / 1e6, 1) if done else None,
             "steps_done": done, "failed": failed, "launch": launch,

@@ -3,7 +3,7 @@ interface height and the capillary-wave dispersion relation.
 
 Test infrastructure only (see ``oracle/__init__``).
 
-Readings (the paper does not say how it measured; each is listed in the design doc):
+Readings (the paper does not say how it measured):
   * bulk pressure p = rho c_s^2 + (G/2) psi^2, the isotropic part of Eq. 20;
   * p_in / rho_in: mean over sites with r < R/2; p_out / rho_out: mean over sites
     with r > R + 0.3 min(nx, ny)/2 (clipped to the lattice);

@@ -23,7 +23,7 @@ lattice is either periodic or bounded by two no-slip walls (Sec. V.B) handled
 with half-way bounce-back; at a wall the missing neighbour psi is taken equal to
 the psi of the adjacent fluid row (a reading: the paper names no wall scheme).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * velocity order e0..e8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
     and the standard D2Q9 transformation matrix M (rows rho, e, zeta, jx, qx, jy, qy,
     pxx, pxy), which the paper uses but does not print;

@@ -41,7 +41,7 @@ def choose_kappa(net, t_over_tc, tau_v, sigma_target, kappa_range=(0.0, 0.95)):
 
 def tune_kappa(lbm, net, t_over_tc, tau_v, sigma_target, tol: float = 0.02,
                max_rounds: int = 4, **laplace_kw):
-    """Choose kappa for each target and verify it with a plain Laplace run (the judge).
+    """Choose kappa for each target and verify it with a plain Laplace run (the check).
 
     Round 0 takes the network's kappa (NaN targets go straight to the fallback) and
     measures sigma at it, all points in one batched run. Points that miss by more than

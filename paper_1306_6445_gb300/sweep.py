@@ -1,5 +1,5 @@
 """Laplace-law measurements of many droplets at once (batched lattices), the training data
-and the judge of the surrogate network.
+and the check of the surrogate network.
 
 Each point (T/T_c, kappa, tau_v) becomes one periodic side x side lattice of the
 Carnahan-Starling fluid (a = 1, b = 4, R = 1, G = -1, sigma_F = 0.087 in Eq. 8, MRT rates

@@ -3,8 +3,8 @@
 Laplace measurements use the oracle's reading of the method (tests may use the oracle);
 every run is converged (the droplets change by < 1e-5 over the last chunks of these
 step counts). Tolerances state how far the paper's own numbers can be expected to be
-matched given the readings listed in the design doc (relaxation rates other than s_v and the
-measurement masks are not given in the paper)."""
+matched given the readings of the paper's silences (relaxation rates other than s_v and
+the measurement masks are not given in the paper)."""
 import json
 import os
 

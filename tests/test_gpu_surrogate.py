@@ -1,7 +1,7 @@
 """The surrogate end to end on the GPU: batched Laplace measurements of 512 droplets train
 the network (the library's own kernels), the network picks kappa for target surface
 tensions at (T/T_c, tau_v) it was not shown, and a plain Laplace run at that kappa (the
-judge) lands within 2 % of the target. What the network gains over the method without it
+check) lands within 2 % of the target. What the network gains over the method without it
 is measured against the Laplace-law route of Eq. 22 (a kappa = 0 calibration run, then
 kappa = 1 - sigma*/sigma_0): no calibration run, and a smaller miss."""
 import numpy as np
@@ -66,11 +66,11 @@ def test_target_sigma_within_2_percent_without_calibration(lbm, trained):
 
     g = target_grid()
     res = surrogate.tune_kappa(lbm, trained, g[:, 0], g[:, 1], g[:, 2], tol=0.02)
-    # the network alone was right everywhere: one Laplace run (the judge) per target
+    # the network alone was right everywhere: one Laplace run (the check) per target
     assert np.all(res["runs"] == 1)
     assert np.max(np.abs(res["rel_err"])) < 0.02
     # the method without the network: a kappa = 0 run per (T, tau), the law of Eq. 22,
-    # then the judge
+    # then the check
     s0 = surrogate.sweep_points(lbm, g[:, 0], np.zeros(len(g)), g[:, 1])
     k_law = 1 - g[:, 2] / s0
     s_law = surrogate.sweep_points(lbm, g[:, 0], k_law, g[:, 1])
