@@ -362,6 +362,7 @@ lb_status lb_set_launch(lb_ctx *c, int variant, int rows) {
 }
 
 lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
+    const lbm::NvtxRange nvtx_range("lb_autotune");
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (trial_steps < 1) return fail(c, LB_EINVAL, "lb_autotune: trial_steps < 1");
@@ -479,6 +480,7 @@ lb_status lb_set_rho_u(lb_ctx *c, const double *rho, const double *ux, const dou
 }
 
 lb_status lb_step(lb_ctx *c, int n) {
+    const lbm::NvtxRange nvtx_range("lb_step");
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (n < 0) return fail(c, LB_EINVAL, "lb_step: n < 0");
@@ -554,6 +556,7 @@ lb_status lb_set_populations(lb_ctx *c, const void *src, size_t bytes) {
 }
 
 lb_status lb_reduce(lb_ctx *c, double out[4]) {
+    const lbm::NvtxRange nvtx_range("lb_reduce");
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (!out) return fail(c, LB_EINVAL, "lb_reduce: NULL");
@@ -571,6 +574,7 @@ lb_status lb_reduce(lb_ctx *c, double out[4]) {
 }
 
 lb_status lb_measure_droplet(lb_ctx *c, double radius, double out[8]) {
+    const lbm::NvtxRange nvtx_range("lb_measure_droplet");
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (!out) return fail(c, LB_EINVAL, "lb_measure_droplet: NULL");
@@ -590,6 +594,7 @@ lb_status lb_measure_droplet(lb_ctx *c, double radius, double out[8]) {
 }
 
 lb_status lb_interface_height(lb_ctx *c, double rho_mid, double *heights) {
+    const lbm::NvtxRange nvtx_range("lb_interface_height");
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (!heights) return fail(c, LB_EINVAL, "lb_interface_height: NULL");

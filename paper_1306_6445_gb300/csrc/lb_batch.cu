@@ -442,6 +442,7 @@ lb_status lb_batch_set_rho_u(lb_batch *b, int i, const double *rho, const double
 }
 
 lb_status lb_batch_step(lb_batch *b, int n) {
+    const lbm::NvtxRange nvtx_range("lb_batch_step");
     if (!b || n < 0) return LB_EINVAL;
     if (b->sticky != LB_OK) return b->sticky;
     while (n >= kGraphSteps) {
@@ -495,6 +496,7 @@ lb_status lb_batch_get_populations(lb_batch *b, int i, void *dst, size_t bytes) 
 }
 
 lb_status lb_batch_measure(lb_batch *b, const double *radius, double *out) {
+    const lbm::NvtxRange nvtx_range("lb_batch_measure");
     if (!b || !radius || !out) return LB_EINVAL;
     if (b->sticky != LB_OK) return b->sticky;
     LB_BCUDA(b, cudaMemcpyAsync(b->d_radius, radius, b->n * sizeof(double), cudaMemcpyHostToDevice,

@@ -7,9 +7,20 @@
 
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb.h"
 
 namespace lbm {
+
+// NVTX range over the host side of an entry point (named in profiler timelines; a few
+// nanoseconds when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Error bits written by kernels into the context's device flag word.
 enum : int { ERR_DOMAIN = 1, ERR_TIMEOUT = 2 };

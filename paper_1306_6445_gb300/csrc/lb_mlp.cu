@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "lb_internal.h"
 #include "lb_mlp.h"
 
 namespace {
@@ -647,6 +648,7 @@ lb_status lb_mlp_loss_grad(lb_mlp *m, float *loss, float *grad) {
 
 lb_status lb_mlp_train(lb_mlp *m, int steps, float lr, float beta1, float beta2, float eps,
                        float *loss) {
+    const lbm::NvtxRange nvtx_range("lb_mlp_train");
     if (!m || steps < 0) return LB_EINVAL;
     if (m->n < 1) return mfail(m, LB_EINVAL, "no training data");
     if (!(lr > 0.f && std::isfinite(lr) && beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f &&
