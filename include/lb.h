@@ -189,6 +189,8 @@ lb_status lb_get_u(lb_ctx *ctx, double *ux, double *uy);
 
 /* Copy the current populations to / from a packed host array [alpha][y][x] of
  * 9*ny*nx elements of the storage type; `bytes` must equal that size exactly.
+ * The array travels as one contiguous copy through the context's spare device buffer,
+ * where a kernel converts between the host layout and the stored state.
  * lb_set_populations resets nothing else (the step counter is kept). Both synchronise.
  * Errors: LB_EINVAL on a size mismatch or NULL, LB_ECUDA. */
 lb_status lb_get_populations(lb_ctx *ctx, void *dst, size_t bytes);

@@ -474,7 +474,7 @@ lb_status lb_set_rho_u(lb_ctx *c, const double *rho, const double *ux, const dou
     LB_CUDA(c, cudaMemcpyAsync(c->d_host_in + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(c, lbm::launch_init_feq(c->prec, c->consts, c->geom, c->d_host_in, c->d_host_in + n,
                                     c->d_host_in + 2 * n, spare(c), c->d_err, c->stream));
-    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], c->stream));
+    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], false, c->stream));
     c->steps = 0;
     return sync_and_check(c);
 }
@@ -535,10 +535,9 @@ lb_status lb_get_populations(lb_ctx *c, void *dst, size_t bytes) {
     const size_t row = (size_t)c->geom.nx * c->elem;
     if (!dst || bytes != 9 * (size_t)c->geom.ny * row)
         return fail(c, LB_EINVAL, "lb_get_populations: NULL or size mismatch");
-    LB_CUDA(c, lbm::launch_stream(c->prec, c->geom, c->f[c->cur], spare(c), c->stream));
-    const char *src = static_cast<const char *>(spare(c)) + lbm::kGhost * c->elem;
-    LB_CUDA(c, cudaMemcpy2DAsync(dst, row, src, (size_t)c->geom.pitch * c->elem, row,
-                                 9 * (size_t)c->geom.ny, cudaMemcpyDeviceToHost, c->stream));
+    // pull into the spare buffer in the host layout, then one contiguous copy
+    LB_CUDA(c, lbm::launch_stream(c->prec, c->geom, c->f[c->cur], spare(c), true, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(dst, spare(c), bytes, cudaMemcpyDeviceToHost, c->stream));
     return sync_and_check(c);
 }
 
@@ -548,10 +547,9 @@ lb_status lb_set_populations(lb_ctx *c, const void *src, size_t bytes) {
     const size_t row = (size_t)c->geom.nx * c->elem;
     if (!src || bytes != 9 * (size_t)c->geom.ny * row)
         return fail(c, LB_EINVAL, "lb_set_populations: NULL or size mismatch");
-    char *dst = static_cast<char *>(spare(c)) + lbm::kGhost * c->elem;
-    LB_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->geom.pitch * c->elem, src, row, row,
-                                 9 * (size_t)c->geom.ny, cudaMemcpyHostToDevice, c->stream));
-    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], c->stream));
+    // one contiguous copy into the spare buffer (host layout), then the kernel unpacks it
+    LB_CUDA(c, cudaMemcpyAsync(spare(c), src, bytes, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, lbm::launch_unstream(c->prec, c->geom, spare(c), c->f[c->cur], true, c->stream));
     return sync_and_check(c);
 }
 

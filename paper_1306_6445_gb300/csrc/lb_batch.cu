@@ -432,7 +432,7 @@ lb_status lb_batch_set_rho_u(lb_batch *b, int i, const double *rho, const double
     LB_BCUDA(b, lbm::launch_init_feq(b->prec, b->consts[i], g, b->d_stage, b->d_stage + n,
                                      b->d_stage + 2 * n, buf(b, i, b->phase ^ 1), b->d_errs + i,
                                      b->stream));
-    LB_BCUDA(b, lbm::launch_unstream(b->prec, g, buf(b, i, b->phase ^ 1), buf(b, i, b->phase),
+    LB_BCUDA(b, lbm::launch_unstream(b->prec, g, buf(b, i, b->phase ^ 1), buf(b, i, b->phase), false,
                                      b->stream));
     LB_BCUDA(b, cudaStreamSynchronize(b->stream));
     int e = 0;
@@ -486,12 +486,11 @@ lb_status lb_batch_get_populations(lb_batch *b, int i, void *dst, size_t bytes) 
     const lbm::Geom &g = b->geom[i];
     const size_t row = (size_t)g.nx * b->elem;
     if (bytes != 9 * (size_t)g.ny * row) return bfail(b, LB_EINVAL, "size mismatch");
-    // the spare buffer of lattice i receives the pulled populations (free between steps)
+    // the spare buffer of lattice i receives the pulled populations in the host layout
+    // (free between steps), then one contiguous copy
     void *spare = buf(b, i, b->phase ^ 1);
-    LB_BCUDA(b, lbm::launch_stream(b->prec, g, buf(b, i, b->phase), spare, b->stream));
-    LB_BCUDA(b, cudaMemcpy2DAsync(dst, row, static_cast<char *>(spare) + lbm::kGhost * b->elem,
-                                  (size_t)g.pitch * b->elem, row, 9 * (size_t)g.ny,
-                                  cudaMemcpyDeviceToHost, b->stream));
+    LB_BCUDA(b, lbm::launch_stream(b->prec, g, buf(b, i, b->phase), spare, true, b->stream));
+    LB_BCUDA(b, cudaMemcpyAsync(dst, spare, bytes, cudaMemcpyDeviceToHost, b->stream));
     return batch_sync(b);
 }
 

@@ -103,9 +103,10 @@ cudaError_t batch_f64(int variant, int eos, bool configure, int *occ, int grid, 
 // order 0 / 1: visit the row blocks (and the rows inside them) forward / in reverse
 cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,
                         const void *tensor_map_in, void *gout, int *err, cudaStream_t stream);
-cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf,
+// packed: f in the host layout [a][y][x] (no pitch, no ghosts) instead of the padded one
+cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, bool packed,
                             cudaStream_t stream);
-cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f,
+cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f, bool packed,
                           cudaStream_t stream);
 cudaError_t launch_init_feq(int prec, const Consts &c, const Geom &g, const double *rho,
                             const double *ux, const double *uy, void *f, int *err,

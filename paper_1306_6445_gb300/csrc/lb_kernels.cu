@@ -19,11 +19,21 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 // ---------------------------------------------------------------- permutations
 
+// Element of population b at (x, y) in f: the padded layout (pitch, ghost offset), or,
+// PACKED, the host layout [b][y][x] without padding.
+template <bool PACKED>
+__device__ __forceinline__ long long f_index(int b, int x, int y, int nx, int ny, int pitch,
+                                             long long plane) {
+    if (PACKED) return ((long long)b * ny + y) * nx + x;
+    return b * plane + (long long)y * pitch + x + GH;
+}
+
 // g_b(y) = f_b(y + e_b) where y + e_b is inside the lattice, else f_opp(b)(y) at a wall
 // (inverse of the pull with bounce-back); a population leaving through an open boundary
-// (BC 2) is not pulled back by any site and keeps f_b(y). f and g use the padded layout;
-// the ghost columns of g are written (periodic images, or copies of the edge columns).
-template <typename T, int BC>
+// (BC 2) is not pulled back by any site and keeps f_b(y). g uses the padded layout and its
+// ghost columns are written (periodic images, or copies of the edge columns); f is padded
+// or packed (PACKED).
+template <typename T, int BC, bool PACKED>
 __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, int ny, int pitch,
                            long long plane) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,13 +44,13 @@ __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, i
         int ty = y + EYv(b), tx = x + EXv(b);
         T v;
         if ((BC != 0 && ty < 0) || (BC == 1 && ty >= ny)) {
-            v = f[opp(b) * plane + (long long)y * pitch + x + GH];
+            v = f[f_index<PACKED>(opp(b), x, y, nx, ny, pitch, plane)];
         } else if (BC == 2 && (ty >= ny || tx < 0 || tx >= nx)) {
-            v = f[b * plane + (long long)y * pitch + x + GH];
+            v = f[f_index<PACKED>(b, x, y, nx, ny, pitch, plane)];
         } else {
             if (BC == 0) ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
             tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
-            v = f[b * plane + (long long)ty * pitch + tx + GH];
+            v = f[f_index<PACKED>(b, tx, ty, nx, ny, pitch, plane)];
         }
         T *rowg = g + b * plane + (long long)y * pitch;
         rowg[x + GH] = v;
@@ -54,8 +64,9 @@ __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, i
     }
 }
 
-// f_a(x) = pull of g (the populations of the current time), padded layout, no ghosts.
-template <typename T, int BC>
+// f_a(x) = pull of g (the populations of the current time), into the padded layout (no
+// ghosts) or, PACKED, the host layout.
+template <typename T, int BC, bool PACKED>
 __global__ void k_stream(const T *__restrict__ g, T *__restrict__ f, int nx, int ny, int pitch,
                          long long plane) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,7 +74,7 @@ __global__ void k_stream(const T *__restrict__ g, T *__restrict__ f, int nx, int
     const int y = (int)(i / nx), x = (int)(i % nx);
 #pragma unroll
     for (int a = 0; a < 9; ++a)
-        f[a * plane + (long long)y * pitch + x + GH] =
+        f[f_index<PACKED>(a, x, y, nx, ny, pitch, plane)] =
             pull_global<T, BC>(g, a, x, y, nx, ny, pitch, plane);
 }
 
@@ -416,11 +427,20 @@ cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaun
     return step_f64(c, g, l, order, tensor_map_in, gout, err, st, false);
 }
 
-cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, cudaStream_t st) {
+cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, bool packed,
+                            cudaStream_t st) {
     const unsigned nb = blocks_for((long long)g.nx * g.ny, 256);
-#define LB_UNS(T, W)                                                                          \
-    k_unstream<T, W><<<nb, 256, 0, st>>>(static_cast<const T *>(f), static_cast<T *>(gbuf), g.nx, \
-                                         g.ny, g.pitch, g.plane)
+#define LB_UNS(T, W)                                                                           \
+    do {                                                                                       \
+        if (packed)                                                                            \
+            k_unstream<T, W, true><<<nb, 256, 0, st>>>(static_cast<const T *>(f),              \
+                                                       static_cast<T *>(gbuf), g.nx, g.ny,     \
+                                                       g.pitch, g.plane);                      \
+        else                                                                                   \
+            k_unstream<T, W, false><<<nb, 256, 0, st>>>(static_cast<const T *>(f),             \
+                                                        static_cast<T *>(gbuf), g.nx, g.ny,    \
+                                                        g.pitch, g.plane);                     \
+    } while (0)
     if (prec == LB_FP32) {
         BC3(LB_UNS, float);
     } else if (prec == LB_BF16) {
@@ -432,11 +452,20 @@ cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f, cudaStream_t st) {
+cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f, bool packed,
+                          cudaStream_t st) {
     const unsigned nb = blocks_for((long long)g.nx * g.ny, 256);
-#define LB_STR(T, W)                                                                         \
-    k_stream<T, W><<<nb, 256, 0, st>>>(static_cast<const T *>(gbuf), static_cast<T *>(f), g.nx, \
-                                       g.ny, g.pitch, g.plane)
+#define LB_STR(T, W)                                                                           \
+    do {                                                                                       \
+        if (packed)                                                                            \
+            k_stream<T, W, true><<<nb, 256, 0, st>>>(static_cast<const T *>(gbuf),             \
+                                                     static_cast<T *>(f), g.nx, g.ny, g.pitch, \
+                                                     g.plane);                                 \
+        else                                                                                   \
+            k_stream<T, W, false><<<nb, 256, 0, st>>>(static_cast<const T *>(gbuf),            \
+                                                      static_cast<T *>(f), g.nx, g.ny,         \
+                                                      g.pitch, g.plane);                       \
+    } while (0)
     if (prec == LB_FP32) {
         BC3(LB_STR, float);
     } else if (prec == LB_BF16) {

@@ -211,6 +211,44 @@ def test_checkpoint_resume_is_bit_identical(lbm):
         lat.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("bc", ["periodic", "walls", "open"])
+def test_page_locked_and_pageable_host_buffers_give_the_same_bits(lbm, prec, bc):
+    """lb_get_populations, lb_set_populations and lb_get_rho give the same bits with
+    page-locked host buffers (the bench's end-to-end path) as with pageable ones."""
+    if prec == "bf16" and bc == "open":
+        pytest.skip("open boundaries are not compiled for BF16 storage")
+    eos, G, _ = case_params(lbm, "cs")
+    rv, rl, _ = lbm.lb_maxwell(eos, G)
+    kw = {"walls_y": True} if bc == "walls" else ({"open_bc": True} if bc == "open" else {})
+    nx, ny = 131, 67
+    mk = lambda: lbm.Lattice(nx, ny, eos, G, kappa=0.3, rates=lbm.RateParams.from_viscosity(0.1),
+                             prec=prec, storage_shift=rv, **kw)
+    lat = mk()
+    lat.set_rho_u(I.droplet_density(nx, ny, 15.0, rl, rv))
+    lat.step(7)
+    tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.int16}[prec]
+    pinned = torch.empty((9, ny, nx), dtype=tdt, pin_memory=True)
+    lbm.lb_get_populations(lat.ctx, pinned.data_ptr(), pinned.numel() * pinned.element_size())
+    f_pageable = lat.populations()
+    assert np.array_equal(pinned.numpy().view(f_pageable.dtype), f_pageable)
+    rho_pinned = torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    lbm.lb_get_rho(lat.ctx, rho_pinned)
+    assert np.array_equal(rho_pinned, lat.rho())
+    lat.close()
+    outs = []
+    for src in ("pinned", "pageable"):
+        b = mk()
+        if src == "pinned":
+            lbm.lb_set_populations(b.ctx, pinned.data_ptr(), pinned.numel() * pinned.element_size())
+        else:
+            b.set_populations(f_pageable)
+        b.step(3)
+        outs.append(b.populations())
+        b.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_library_owned_buffers_and_default_stream(lbm):
     eos, G, _ = case_params(lbm, "exp")
     rho = I.droplet_density(40, 40, 10.0, 515.0, 80.0)
