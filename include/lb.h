@@ -21,9 +21,10 @@
  *   the context's storage type (double for LB_FP64, float for LB_FP32, and for LB_BF16 the
  *   16-bit stored patterns of f_a - w_a rho_s, see lb_prec).
  * - Populations are stored on the device as 9 planes of ny rows of `pitch`
- *   elements (pitch = lb_pitch(nx, prec) >= nx + 8, a multiple of 32 elements).
- *   Column x of a row sits at element x + 4; elements 2, 3 and nx+4, nx+5 hold
- *   periodic images of columns nx-2, nx-1 and 0, 1. The stored array is the state
+ *   elements (pitch = lb_pitch(nx, prec) >= nx + 2 H, a multiple of 32 elements, with
+ *   H = 8 for LB_FP32 and 4 for LB_FP64 and LB_BF16). Column x of a row sits at element
+ *   x + H; elements H-2, H-1 and nx+H, nx+H+1 hold periodic images of columns nx-2, nx-1
+ *   and 0, 1 (copies of the edge columns for LB_BC_OPEN). The stored array is the state
  *   g from which the populations of the current time are PULLED,
  *   f_a(x, t) = g_a(x - e_a) (bounce-back at walls), i.e. the post-collision values
  *   of the previous step before streaming. lb_get/set_populations convert.

@@ -25,8 +25,12 @@ struct NvtxRange {
 // Error bits written by kernels into the context's device flag word.
 enum : int { ERR_DOMAIN = 1, ERR_TIMEOUT = 2 };
 
-// Ghost columns in front of column 0 of every stored row (periodic images live there).
-constexpr int kGhost = 4;
+// Elements in front of column 0 of every stored row (the last two hold periodic images or
+// edge copies). FP32 uses 8, so that column 0 sits 32 bytes into the row and each warp's
+// 64-column store covers whole 32-byte sectors; the TMA box (columns x0 - 4 ..) then starts
+// at element x0 + 4, still 16-byte aligned. FP64 rows are sector-aligned with 4 already,
+// and BF16 keeps 4 because its box start must stay a multiple of 8 elements.
+constexpr int ghost_of_prec(int prec) { return prec == LB_FP32 ? 8 : 4; }
 
 // Per-lattice constants of the update, in double; kernels convert them to their type.
 struct Consts {
@@ -52,7 +56,7 @@ struct Consts {
 // Geometry of one lattice's device population buffer.
 struct Geom {
     int nx, ny;
-    int pitch;          // elements per stored row (>= nx + 2 * kGhost, multiple of 32)
+    int pitch;          // elements per stored row (>= nx + 2 * ghost, multiple of 32)
     long long plane;    // elements per population plane = ny * pitch
     int walls;          // boundary kind (lb_bc): 0 periodic, 1 walls in y, 2 open (see lb.h)
 };

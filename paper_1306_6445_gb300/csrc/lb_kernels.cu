@@ -21,11 +21,11 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 // Element of population b at (x, y) in f: the padded layout (pitch, ghost offset), or,
 // PACKED, the host layout [b][y][x] without padding.
-template <bool PACKED>
+template <typename T, bool PACKED>
 __device__ __forceinline__ long long f_index(int b, int x, int y, int nx, int ny, int pitch,
                                              long long plane) {
     if (PACKED) return ((long long)b * ny + y) * nx + x;
-    return b * plane + (long long)y * pitch + x + GH;
+    return b * plane + (long long)y * pitch + x + GH<T>;
 }
 
 // g_b(y) = f_b(y + e_b) where y + e_b is inside the lattice, else f_opp(b)(y) at a wall
@@ -44,22 +44,22 @@ __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, i
         int ty = y + EYv(b), tx = x + EXv(b);
         T v;
         if ((BC != 0 && ty < 0) || (BC == 1 && ty >= ny)) {
-            v = f[f_index<PACKED>(opp(b), x, y, nx, ny, pitch, plane)];
+            v = f[f_index<T, PACKED>(opp(b), x, y, nx, ny, pitch, plane)];
         } else if (BC == 2 && (ty >= ny || tx < 0 || tx >= nx)) {
-            v = f[f_index<PACKED>(b, x, y, nx, ny, pitch, plane)];
+            v = f[f_index<T, PACKED>(b, x, y, nx, ny, pitch, plane)];
         } else {
             if (BC == 0) ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
             tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
-            v = f[f_index<PACKED>(b, tx, ty, nx, ny, pitch, plane)];
+            v = f[f_index<T, PACKED>(b, tx, ty, nx, ny, pitch, plane)];
         }
         T *rowg = g + b * plane + (long long)y * pitch;
-        rowg[x + GH] = v;
+        rowg[x + GH<T>] = v;
         if (BC == 2) {
-            if (x == 0) rowg[GH - 1] = rowg[GH - 2] = v;
-            if (x == nx - 1) rowg[nx + GH] = rowg[nx + GH + 1] = v;
+            if (x == 0) rowg[GH<T> - 1] = rowg[GH<T> - 2] = v;
+            if (x == nx - 1) rowg[nx + GH<T>] = rowg[nx + GH<T> + 1] = v;
         } else {
-            if (x < 2) rowg[nx + GH + x] = v;
-            if (x >= nx - 2) rowg[x - nx + GH] = v;
+            if (x < 2) rowg[nx + GH<T> + x] = v;
+            if (x >= nx - 2) rowg[x - nx + GH<T>] = v;
         }
     }
 }
@@ -74,7 +74,7 @@ __global__ void k_stream(const T *__restrict__ g, T *__restrict__ f, int nx, int
     const int y = (int)(i / nx), x = (int)(i % nx);
 #pragma unroll
     for (int a = 0; a < 9; ++a)
-        f[f_index<PACKED>(a, x, y, nx, ny, pitch, plane)] =
+        f[f_index<T, PACKED>(a, x, y, nx, ny, pitch, plane)] =
             pull_global<T, BC>(g, a, x, y, nx, ny, pitch, plane);
 }
 
@@ -109,7 +109,7 @@ __global__ void k_init_feq(const double *__restrict__ rho, const double *__restr
     o[6] = bd - m[3] * i6 - m[4] * i12 + m[5] * i6 + m[6] * i12 - m[8] * 0.25;
     o[7] = bd - m[3] * i6 - m[4] * i12 - m[5] * i6 - m[6] * i12 + m[8] * 0.25;
     o[8] = bd + m[3] * i6 + m[4] * i12 - m[5] * i6 - m[6] * i12 - m[8] * 0.25;
-    T *p = f + (long long)y * pitch + x + GH;
+    T *p = f + (long long)y * pitch + x + GH<T>;
 #pragma unroll
     for (int a = 0; a < 9; ++a) p[a * plane] = pop_enc<T>(Arith<T>(o[a]), a, P);
 }

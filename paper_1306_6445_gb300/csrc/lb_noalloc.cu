@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "lb_device.cuh"
 #include "lb_internal.h"
@@ -35,7 +36,8 @@ constexpr int NA_DOUBLES = NA_ERR + 4;
 // The scratch: 4104 doubles (32.8 KB) per GPU, shared by every call.
 static __device__ __align__(256) double lb_noalloc_scratch[NA_DOUBLES];
 
-constexpr int GHOST = lbm::kGhost;
+template <typename T>
+constexpr int GHOST = lbm::ghost_of_prec(std::is_same<T, float>::value ? LB_FP32 : LB_FP64);
 
 __device__ __forceinline__ int na_opp(int a) {
     return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
@@ -52,11 +54,11 @@ template <typename T, bool WALLS>
 __device__ __forceinline__ T na_pull(const T *__restrict__ g, int a, int x, int y, int nx, int ny,
                                      int pitch, long long plane) {
     int sy = y - na_ey(a);
-    if (WALLS && (sy < 0 || sy >= ny)) return g[na_opp(a) * plane + (long long)y * pitch + x + GHOST];
+    if (WALLS && (sy < 0 || sy >= ny)) return g[na_opp(a) * plane + (long long)y * pitch + x + GHOST<T>];
     if (!WALLS) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
     int sx = x - na_ex(a);
     sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-    return g[a * plane + (long long)sy * pitch + sx + GHOST];
+    return g[a * plane + (long long)sy * pitch + sx + GHOST<T>];
 }
 
 template <typename T, bool WALLS>

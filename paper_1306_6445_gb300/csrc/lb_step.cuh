@@ -15,12 +15,14 @@
 // reads each population once and writes it once, with aligned, site-local stores.
 //
 // Each population plane has ny rows of `pitch` elements. Column x of the lattice lives at
-// element x + GH of its row (GH = 4); elements 2, 3 and nx+4, nx+5 are ghost copies of
-// columns nx-2, nx-1 and 0, 1 (periodic images), rewritten by every kernel that writes g.
+// element x + GH<T> of its row (8 for float storage, 4 otherwise); elements GH-2, GH-1 and
+// nx+GH, nx+GH+1 are ghost copies of columns nx-2, nx-1 and 0, 1 (periodic images),
+// rewritten by every kernel that writes g.
 //
 // Hot kernel (k_pull_collide): a CTA owns a strip of TX columns (two per thread) and
-// marches up `rows` rows. Rows of g (9 planes x (TX + 8) columns, i.e. the strip plus a
-// 4-column apron on each side) arrive through a ring of S shared-memory stages fed by
+// marches up `rows` rows. Rows of g (9 planes x (TX + AL + 4) columns, i.e. the strip plus an
+// apron of AL columns on the left, 8 for float storage and 4 otherwise, and 4 on the right)
+// arrive through a ring of S shared-memory stages fed by
 // 3-D TMA loads (cp.async.bulk.tensor) completing on per-stage mbarriers. From the ring a
 // thread pulls f for its two sites, forms rho and psi (psi is never stored in HBM; a
 // four-row psi ring with one halo column on each side lives in shared memory), then
@@ -45,7 +47,16 @@ namespace lbm {
 
 namespace {
 
-constexpr int GH = 4;  // ghost columns before column 0 of each row
+// elements before column 0 of each row (ghost_of_prec of the storage type)
+template <typename T>
+constexpr int GH = std::is_same<T, float>::value ? 8 : 4;
+// ring rows of the step kernel: a strip of TX columns with AL<T> apron columns on the left
+// and 4 on the right, so the TMA box starts at column x0 - AL<T>, i.e. at element x0 of the
+// row (aligned like x0 itself), and ring column = x - x0 + AL<T>
+template <typename T>
+constexpr int AL = GH<T>;
+template <typename T, int TX>
+constexpr int ring_width() { return TX + AL<T> + 4; }
 constexpr int RED_THREADS = 256;      // reduction blocks (diagnostics, batch measurement)
 constexpr int RED_MAX_BLOCKS = 1024;
 
@@ -152,13 +163,13 @@ __device__ __forceinline__ T pull_global(const T *__restrict__ g, int a, int x, 
     const int ex = EXv(a), ey = EYv(a);
     int sy = y - ey;
     if ((BC != 0 && sy < 0) || (BC == 1 && sy >= ny))
-        return g[opp(a) * plane + (long long)y * pitch + x + GH];
+        return g[opp(a) * plane + (long long)y * pitch + x + GH<T>];
     if (BC == 0) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
     if (BC == 2) sy = sy >= ny ? ny - 1 : sy;
     int sx = x - ex;
     if (BC == 2) sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
     else sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-    return g[a * plane + (long long)sy * pitch + sx + GH];
+    return g[a * plane + (long long)sy * pitch + sx + GH<T>];
 }
 
 // the value of f_a(x, y) (decoded from the storage type)
@@ -191,7 +202,7 @@ __host__ __device__ constexpr int psi_ring_rows() { return G == 1 ? 4 : 8; }
 // the psi ring, then S mbarriers
 template <typename T, int TX, int S, int G>
 __host__ __device__ constexpr size_t step_bar_offset() {
-    return (size_t)S * (((9u * (TX + 8) * sizeof(T)) + 127u) / 128u * 128u) +
+    return (size_t)S * (((9u * ring_width<T, TX>() * sizeof(T)) + 127u) / 128u * 128u) +
            (((size_t)psi_ring_rows<G>() * (TX + 4) * sizeof(Arith<T>) + 15u) / 16u * 16u);
 }
 template <typename T, int TX, int S, int G>
@@ -330,9 +341,11 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
     static_assert(G == 1 || G == 2, "one or two row groups");
     constexpr bool WALLS = BC != 0;   // rows outside the lattice are not periodic images
     static_assert(S >= G + 4, "ring rows of one iteration plus one row in flight");
-    static_assert(TX % 4 == 0 && TX + 8 <= 256, "TMA box: 16-byte aligned start, at most 256 columns");
+    static_assert(TX % 4 == 0 && ring_width<T, TX>() <= 256,
+                  "TMA box: 16-byte aligned start, at most 256 columns");
     constexpr int NT = TX / 2;      // threads per row group
-    constexpr int BW = TX + 8;      // ring row: columns x0-4 .. x0+TX+3 -> ring col = x - x0 + 4
+    constexpr int L = AL<T>;        // left apron
+    constexpr int BW = ring_width<T, TX>();   // ring row: columns x0-L .. x0+TX+3 -> col x - x0 + L
     constexpr int RW = TX + 4;      // psi row: columns x0-2 .. x0+TX+1 -> psi col = x - x0 + 2
     constexpr int PR = psi_ring_rows<G>();
     constexpr uint32_t STAGE_BYTES = 9u * BW * sizeof(T);
@@ -364,6 +377,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             // TMA unit and never read (bounce-back replaces those links)
             const int gy = WALLS ? r : ((r % ny) + ny) % ny;
             mbar_arrive_expect_tx(&bar[sl], STAGE_BYTES);
+            // element x0 holds column x0 - L, the first of the box
             tma_load_3d(ring + sl * STAGE_ELEMS, tmap, x0, gy, 0, &bar[sl]);
         }
     };
@@ -385,7 +399,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                                   : Ring<T>{stage(j + 1), stage(j), stage(j - 1)};
         const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
         if (act) {
-            pull2<T, BC, BW, true>(keep, r, c0 + 4, c0 + 5, bottom, top, P);
+            pull2<T, BC, BW, true>(keep, r, c0 + L, c0 + L + 1, bottom, top, P);
             const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
             if (both) {
                 store_pair<A>(ps + c0 + 2, psi, true);
@@ -395,10 +409,10 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
         }
         if (t == NT - 1) {   // the two halo columns x0-1 and x0+w as one packed pair
             V2<A> h[9];
-            int ha = 3, hb = w + 4;
+            int ha = L - 1, hb = w + L;
             if (BC == 2) {   // open sides: psi beyond the lattice is that of its edge column
-                if (x0 == 0) ha = 4;
-                if (x0 + w == nx) hb = w + 3;
+                if (x0 == 0) ha = L;
+                if (x0 + w == nx) hb = w + L - 1;
             }
             pull2<T, BC, BW, false>(h, r, ha, hb, bottom, top, P);
             const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
@@ -465,7 +479,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             collide_pair<A, BC == 2>(fc, pn, P);
 
             const int x = x0 + c0;
-            const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH);
+            const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH<T>);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
                 store_pop_pair<T>(gout + (idx + a * plane), fc[a], both, a, P);
@@ -477,9 +491,9 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                     for (int a = 0; a < 9; ++a) {
                         const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
                         T *rb = gout + (rowi + a * plane);
-                        if (x == 0) rb[GH - 1] = rb[GH - 2] = v0;
-                        if (x == nx - 1) rb[nx + GH] = rb[nx + GH + 1] = v0;
-                        if (both && x + 1 == nx - 1) rb[nx + GH] = rb[nx + GH + 1] = v1;
+                        if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
+                        if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
+                        if (both && x + 1 == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v1;
                     }
                 }
             } else if (x < 2 || x + 1 >= nx - 2) {
@@ -489,10 +503,10 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                 for (int a = 0; a < 9; ++a) {
                     const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
                     T *rb = gout + (rowi + a * plane);
-                    if (x < 2) rb[nx + GH + x] = v0;
-                    if (both && x + 1 < 2) rb[nx + GH + x + 1] = v1;
-                    if (x >= nx - 2) rb[x - nx + GH] = v0;
-                    if (both && x + 1 >= nx - 2) rb[x + 1 - nx + GH] = v1;
+                    if (x < 2) rb[nx + GH<T> + x] = v0;
+                    if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
+                    if (x >= nx - 2) rb[x - nx + GH<T>] = v0;
+                    if (both && x + 1 >= nx - 2) rb[x + 1 - nx + GH<T>] = v1;
                 }
             }
         }

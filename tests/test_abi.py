@@ -48,8 +48,11 @@ def test_library_exports_every_declared_symbol(lbm):
 
 
 def test_pitch_and_buffer_size(lbm):
-    # nx + 8 ghost/apron columns, rounded up to 32 elements
+    # nx + 2 H elements (H = 8 for FP32, 4 otherwise), rounded up to 32 elements
     assert lbm.lb_pitch(1, lbm.LB_FP32) == 32
+    assert lbm.lb_pitch(2033, lbm.LB_FP32) == 2080
+    assert lbm.lb_pitch(2033, lbm.LB_FP64) == 2048
+    assert lbm.lb_pitch(2033, lbm.LB_BF16) == 2048
     assert lbm.lb_pitch(2048, lbm.LB_FP64) == 2080
     assert lbm.lb_pitch(2024, lbm.LB_FP32) == 2048
     assert lbm.lb_buffer_bytes(100, 7, lbm.LB_FP64) == 9 * 7 * 128 * 8
