@@ -192,7 +192,9 @@ def time_precision(lbm, torch, inputs, prec, nx, ny, inner, steps, warmup, dist,
     if launch is not None and launch[0] >= 0:
         lbm.lb_set_launch(lat.ctx, launch[0], launch[1])
     else:
-        lat.autotune(5)          # the library's own launch autotuner (state unchanged)
+        # the library's own launch autotuner (state unchanged); 20 launches per timed run
+        # separate candidates about 1 % apart, FP64 launches are 30x longer
+        lat.autotune(3 if prec == "fp64" else 20)
     shape = lbm.lb_get_launch(lat.ctx)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):

@@ -147,7 +147,7 @@ lb_status lb_set_storage_shift(lb_ctx *ctx, double rho_s);
 lb_status lb_set_launch(lb_ctx *ctx, int variant, int rows);
 
 /* Autotuner: time every compiled variant with rows per CTA from {default, 6, 8, 9, 10,
- * 11, 12, 14, 16, 20, 24} (at most ny) on this lattice and keep the fastest. Each
+ * 11, 12, 13, 14, 15, 16, 20, 24} (at most ny) on this lattice and keep the fastest. Each
  * candidate runs one untimed launch and then three timed runs of `trial_steps` >= 1
  * launches (its time is the fastest run) of the step kernel
  * that read the current state and write the spare buffer, so the state and the step

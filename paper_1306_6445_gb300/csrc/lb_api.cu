@@ -368,7 +368,7 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
     if (s != LB_OK) return s;
     if (trial_steps < 1) return fail(c, LB_EINVAL, "lb_autotune: trial_steps < 1");
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
-    static const int cand[] = {0, 6, 8, 9, 10, 11, 12, 14, 16, 20, 24};
+    static const int cand[] = {0, 6, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LB_CUDA(c, cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
