@@ -149,7 +149,8 @@ lb_status lb_set_launch(lb_ctx *ctx, int variant, int rows);
 /* Autotuner: time every compiled variant with rows per CTA from {default, 6, 8, 9, 10,
  * 11, 12, 13, 14, 15, 16, 20, 24} (at most ny) on this lattice and keep the fastest. Each
  * candidate runs one untimed launch and then three timed runs of `trial_steps` >= 1
- * launches (its time is the fastest run) of the step kernel
+ * launches (its time is the fastest run; the launches alternate the visiting order as
+ * lb_step does) of the step kernel
  * that read the current state and write the spare buffer, so the state and the step
  * count are unchanged. Per-site results do not depend on the choice. Writes the choice
  * if the pointers are not NULL. Synchronises. Errors: LB_EINVAL, LB_ECUDA, and the

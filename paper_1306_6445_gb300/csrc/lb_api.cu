@@ -387,10 +387,15 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
             for (int i = 0; i < n_tried; ++i) seen |= tried_rows[i] == rr;
             if (seen) continue;
             tried_rows[n_tried++] = rr;
+            // consecutive trial launches alternate the visiting order like lb_step does,
+            // so each one starts on the rows the previous one touched last (in L2)
+            int order = 0;
             auto once = [&]() {
-                return lbm::launch_step(c->prec, c->consts, c->geom, c->launch, 0,
-                                        &c->tmap[c->cur], c->f[c->cur ^ 1], c->d_err,
-                                        c->stream);
+                const cudaError_t r = lbm::launch_step(c->prec, c->consts, c->geom, c->launch,
+                                                       order, &c->tmap[c->cur],
+                                                       c->f[c->cur ^ 1], c->d_err, c->stream);
+                order ^= 1;
+                return r;
             };
             e = once();
             // best of three timed runs: a single short run is at the mercy of clock and

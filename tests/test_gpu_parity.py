@@ -151,6 +151,7 @@ def test_full_size_step_sampled_against_oracle(lbm, prec, nx, ny, walls):
     lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.6, sigma_force=0.02, rates=rates, prec=prec,
                       walls_y=walls)
     lat.set_rho_u(rho, ux, uy)
+    lat.autotune(3)                  # the launch the benchmark would choose
     f0 = lat.populations().astype(np.float64)
     lat.step(1)
     got = lat.populations()
