@@ -595,15 +595,17 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
     grid_dependency_wait();
     grid_dependents_launch();
     for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
-        const BatchItem it = items[i];
+        // phase 1 (every other step) visits the items, and the rows inside each, in reverse:
+        // a step then starts on the rows the previous one wrote last (still in L2)
+        const BatchItem it = items[phase ? n_items - 1 - i : i];
         const BatchLattice<T> &L = lats[it.lat];
         const DevConsts<Arith<T>> P = L.P;
         const CUtensorMap *map = maps + 2 * it.lat + phase;
         if (threadIdx.x == 0) prefetch_tensormap(map);
         bool bad = false;
         const int st = march<T, EOS, false, TX, S, G>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
-                                                   L.plane, it.x0, it.w, it.yb, it.n, it.dir,
-                                                   smem_raw, bad);
+                                                   L.plane, it.x0, it.w, it.yb, it.n,
+                                                   phase ? -it.dir : it.dir, smem_raw, bad);
         if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
         if (st) {
             if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
