@@ -149,9 +149,11 @@ lb_status lb_set_launch(lb_ctx *ctx, int variant, int rows);
 /* Autotuner: time every compiled variant with rows per CTA from {default, 6, 8, 9, 10,
  * 11, 12, 13, 14, 15, 16, 20, 24} (at most ny) on this lattice and keep the fastest. Each
  * candidate runs one untimed launch and then three timed runs of `trial_steps` >= 1
- * launches (its time is the fastest run; the launches alternate the visiting order as
- * lb_step does) of the step kernel
- * that read the current state and write the spare buffer, so the state and the step
+ * launches (its time is the fastest run). The trial launches take real steps on a scratch
+ * copy of the state (a temporary device buffer of lb_buffer_bytes, freed before return),
+ * ping-ponging with the spare buffer in the alternating visiting order of lb_step, so every
+ * candidate meets the cache reuse of real stepping; without memory for the copy they read
+ * the state and write the spare buffer. The state is only read, so the state and the step
  * count are unchanged. Per-site results do not depend on the choice. Writes the choice
  * if the pointers are not NULL. Synchronises. Errors: LB_EINVAL, LB_ECUDA, and the
  * sticky errors of lb_sync. */

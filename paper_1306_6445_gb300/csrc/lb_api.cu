@@ -175,7 +175,7 @@ EncodeTiledFn encode_fn() {
 // 3-D map over one population buffer: (padded column, row, population); one box is a
 // full lattice row of the strip plus its apron: (tx + ghost + 4) x 1 x 9 (the left apron is
 // as wide as the ghost offset, so a box starts at the strip's own first element).
-lb_status make_maps(lb_ctx *c) {
+lb_status encode_map(lb_ctx *c, void *buffer, CUtensorMap *map) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(c, LB_ECUDA, "cuTensorMapEncodeTiled unavailable");
     const Geom &g = c->geom;
@@ -186,15 +186,21 @@ lb_status make_maps(lb_ctx *c) {
     const CUtensorMapDataType dt = c->prec == LB_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : c->prec == LB_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    CUresult r = enc(map, dt, 3, buffer, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return fail(c, LB_ECUDA, buf);
+    }
+    return LB_OK;
+}
+
+lb_status make_maps(lb_ctx *c) {
     for (int b = 0; b < 2; ++b) {
-        CUresult r = enc(&c->tmap[b], dt, 3, c->f[b], dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            char buf[96];
-            std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-            return fail(c, LB_ECUDA, buf);
-        }
+        const lb_status s = encode_map(c, c->f[b], &c->tmap[b]);
+        if (s != LB_OK) return s;
     }
     return LB_OK;
 }
@@ -367,12 +373,29 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
     if (trial_steps < 1) return fail(c, LB_EINVAL, "lb_autotune: trial_steps < 1");
-    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    // device errors of earlier steps are the state's: report them before any trial
+    if ((s = sync_and_check(c)) != LB_OK) return s;
     static const int cand[] = {0, 6, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24};
+    // Trial launches take real steps on a scratch copy of the state, ping-ponging with the
+    // spare buffer as lb_step does (each launch reads what the previous one wrote, in the
+    // alternating visiting order), so every candidate meets the L2 reuse of real stepping;
+    // the state itself is only read. Without room for the copy, every trial reads the
+    // state and writes the spare buffer instead.
+    const size_t bytes = lb_buffer_bytes(c->geom.nx, c->geom.ny, c->prec);
+    void *scratch = nullptr;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        scratch = nullptr;
+    } else if (cudaMemcpyAsync(scratch, c->f[c->cur], bytes, cudaMemcpyDeviceToDevice,
+                               c->stream) != cudaSuccess) {
+        cudaFree(scratch);
+        return fail(c, LB_ECUDA, "lb_autotune: copy of the state failed");
+    }
+    CUtensorMap scratch_map;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    LB_CUDA(c, cudaEventCreate(&e0));
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (scratch) cudaFree(scratch);
         return fail(c, LB_ECUDA, "lb_autotune: cudaEventCreate failed");
     }
     float best_ms = 0.f;
@@ -387,14 +410,19 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
             for (int i = 0; i < n_tried; ++i) seen |= tried_rows[i] == rr;
             if (seen) continue;
             tried_rows[n_tried++] = rr;
-            // consecutive trial launches alternate the visiting order like lb_step does,
-            // so each one starts on the rows the previous one touched last (in L2)
-            int order = 0;
+            if (scratch && (s = encode_map(c, scratch, &scratch_map)) != LB_OK) break;
+            // trial k reads the scratch copy (k even) or the spare buffer (k odd) and
+            // writes the other, in visiting order k & 1
+            int k = 0;
             auto once = [&]() {
+                const bool from_scratch = (k & 1) == 0;
+                const CUtensorMap *src = !scratch       ? &c->tmap[c->cur]
+                                         : from_scratch ? &scratch_map
+                                                        : &c->tmap[c->cur ^ 1];
+                void *dst = (!scratch || from_scratch) ? c->f[c->cur ^ 1] : scratch;
                 const cudaError_t r = lbm::launch_step(c->prec, c->consts, c->geom, c->launch,
-                                                       order, &c->tmap[c->cur],
-                                                       c->f[c->cur ^ 1], c->d_err, c->stream);
-                order ^= 1;
+                                                       k & 1, src, dst, c->d_err, c->stream);
+                ++k;
                 return r;
             };
             e = once();
@@ -421,9 +449,17 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, int *variant, int *rows) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (scratch) cudaFree(scratch);
     if (s != LB_OK) return s;
     if (e != cudaSuccess)
         return fail(c, LB_ECUDA, std::string("lb_autotune: ") + cudaGetErrorString(e));
+    // the trials stepped a copy: a domain error there says nothing about the state; a
+    // timeout (a bounded wait gave up) is kept, it concerns the kernel and not the data
+    int flags = 0;
+    LB_CUDA(c, cudaMemcpy(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags & lbm::ERR_TIMEOUT) return poison(c, LB_ETIMEOUT, "a bounded device-side wait gave up");
+    LB_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     if ((s = apply_launch(c, best_v, best_r)) != LB_OK) return s;
     if (variant) *variant = best_v;
     if (rows) *rows = best_r;
