@@ -609,6 +609,10 @@ def native(args):
     e2e = None
     if not args.no_e2e:
         el, bi, bo = time_e2e(lbm, torch, inputs, nx, ny, inner, K, min(W, 2))
+        if dist is not None:                     # the slowest rank's wall time
+            te = torch.tensor([el], device="cuda")
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            el = float(te.item())
         e2e = {"value": round(world * sites * inner * K / el / 1e6, 1), "unit": "MLUPS",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
