@@ -76,6 +76,13 @@ def parse():
 # helpers
 # --------------------------------------------------------------------------------------
 
+def bench_config(nx, ny, inner, world):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD, "nx": nx, "ny": ny, "lb_steps_per_step": inner,
+            "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -633,9 +640,7 @@ def native(args):
             "steps": K, "warmup": W, "ms_per_step": round(max_ms / K, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "lb_steps_per_step": inner,
-                       "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (2 x 151 MB FP32 population buffers)"},
+            "config": bench_config(nx, ny, inner, world),
             "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary(), "bf16": bf16,
             "batched": batched,
@@ -687,8 +692,9 @@ def reference(args):
         "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": args.nx, "ny": args.ny,
-                   "sample": f"{nx}x{ny} band, 1 LB step per bench step"},
+        "config": dict(bench_config(args.nx, args.ny, args.inner,
+                                    int(os.environ.get("WORLD_SIZE", "1"))),
+                       sample=f"{nx}x{ny} band, 1 LB step per bench step"),
         "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
