@@ -133,3 +133,15 @@ def test_finite_depth_dispersion_tends_to_deep_limit():
 def test_interface_height_linear_interpolation():
     col = np.array([1.0, 1.0, 0.8, 0.4, 0.0, 0.0])
     assert D.interface_height(col, 0.5) == pytest.approx(2.75)
+
+
+def test_splash_weber_numbers_follow_eq22_and_table3():
+    """Sec. V.C's Weber numbers against the rest of the paper: their ratio is the (1 - kappa)
+    scaling of Eq. 22 between kappa = 0 and 0.95, and rho_l U^2 D / We(kappa = 0) is Table 3's
+    surface tension of the same fluid at 1 - kappa = 1 (rho_l of Sec. V.A). This fixes the
+    reading We = rho_l U^2 D / theta with D = 2R that the splash set-up uses."""
+    w, t3, co = GOLD["splash_weber"], GOLD["table3_colosqui"], GOLD["colosqui_coexistence"]
+    k0, k1 = w["kappa"]
+    assert w["We"][1] / w["We"][0] == pytest.approx((1 - k0) / (1 - k1), rel=0.01)
+    theta0 = co["rho_l"] * w["U"] ** 2 * w["D"] / w["We"][0]
+    assert theta0 == pytest.approx(t3["surface_tension"][0], rel=0.02)
