@@ -151,3 +151,21 @@ def test_interface_height_equals_the_oracle_on_the_same_field(lbm, prec, bc):
     h = lat.interface_height(mid)
     lat.close()
     assert np.all(np.isfinite(h)) and abs(np.nanmean(h) - 50.0) < 3.0
+
+
+def test_run_log_records_match_the_library_calls(lbm, tmp_path):
+    from paper_1306_6445_gb300.runlog import run_logged
+
+    eos = lbm.cs_eos(0.8)
+    rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
+    lat = lbm.Lattice(64, 64, eos, -1.0, kappa=0.3, rates=lbm.RateParams.from_viscosity(0.1),
+                      prec="fp32")
+    lat.set_rho_u(I.droplet_density(64, 64, 16.0, rl, rv))
+    recs = run_logged(lat, 30, 10, str(tmp_path / "run.jsonl"), radius=16.0)
+    m = lat.measure_droplet(16.0)
+    red = lat.reduce()
+    lat.close()
+    assert [r["step"] for r in recs] == [10, 20, 30]
+    assert recs[-1]["theta"] == m["theta"] and recs[-1]["rho_in"] == m["rho_in"]
+    assert recs[-1]["mass"] == red[0] and recs[-1]["max_v"] == red[3]
+    assert abs(recs[-1]["mass_drift"]) < 1e-5 and all(r["mlups"] > 0 for r in recs)
