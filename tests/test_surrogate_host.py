@@ -1,0 +1,99 @@
+"""The κ-choice logic of the surrogate's check and fallback (`surrogate.tune_kappa`), on the
+CPU. The Laplace runs are replaced by a synthetic surface tension
+sigma(T, kappa) = sigma_0(T) (1 - kappa)^p, whose exponent p != 1 stands for the departure
+from the leading-order law of Eq. 22 that the paper's Table 2 shows at large kappa. The
+network is a stand-in with a known answer (or none). This checks the bookkeeping:
+one run per target when the network is right; the law, then the secant in
+ln sigma against ln(1 - kappa), otherwise; and failed runs."""
+import numpy as np
+import pytest
+
+from paper_1306_6445_gb300 import surrogate
+
+
+P_EXP = 1.15
+
+
+def sigma0(t):
+    return 0.01 * (1.0 - np.asarray(t)) ** 1.5
+
+
+def fake_sigma(t, kappa):
+    return sigma0(t) * (1.0 - np.asarray(kappa)) ** P_EXP
+
+
+class FakeNet:
+    """invert_kappa returns the exact kappa scaled by `bias` (NaN where `nan_mask`)."""
+
+    def __init__(self, bias=1.0, nan_mask=None):
+        self.bias, self.nan_mask = bias, nan_mask
+
+    def invert_kappa(self, q, lo, hi):
+        t, s = q[:, 0], q[:, 2]
+        k = 1.0 - (s / sigma0(t)) ** (1.0 / P_EXP)
+        k = np.clip(k * self.bias, lo, hi)
+        if self.nan_mask is not None:
+            k = np.where(self.nan_mask, np.nan, k)
+        return k.astype(np.float32)
+
+
+@pytest.fixture
+def runs_log(monkeypatch):
+    calls = []
+
+    def fake_points(lbm, t, kappa, tau, **kw):
+        calls.append(len(t))
+        return fake_sigma(t, kappa)
+
+    monkeypatch.setattr(surrogate, "sweep_points", fake_points)
+    return calls
+
+
+def targets():
+    t = np.array([0.7, 0.8, 0.9, 0.8])
+    kappa_true = np.array([0.3, 0.6, 0.85, 0.93])
+    return t, np.full(4, 0.8), fake_sigma(t, kappa_true), kappa_true
+
+
+def test_a_right_network_needs_one_run_per_target(runs_log):
+    t, tau, s, k = targets()
+    r = surrogate.tune_kappa(None, FakeNet(), t, tau, s, tol=0.02)
+    assert np.all(r["runs"] == 1) and runs_log == [4]
+    assert np.allclose(r["kappa"], k, atol=1e-5)
+    assert np.all(np.abs(r["rel_err"]) < 1e-4)
+
+
+def test_without_a_network_the_law_then_the_secant_reach_the_target(runs_log):
+    t, tau, s, k = targets()
+    r = surrogate.tune_kappa(None, None, t, tau, s, tol=0.005, max_rounds=4)
+    assert np.all(np.abs(r["rel_err"]) <= 0.005)
+    # a kappa = 0 run, the law's kappa, then secant steps: at least 2 runs each, and
+    # the first batched run measured all four at kappa = 0
+    assert np.all(r["runs"] >= 2) and runs_log[0] == 4
+    assert np.allclose(r["kappa"], k, atol=5e-3)
+
+
+def test_a_biased_network_is_caught_by_the_check_and_corrected(runs_log):
+    t, tau, s, k = targets()
+    r = surrogate.tune_kappa(None, FakeNet(bias=0.9), t, tau, s, tol=0.01)
+    assert np.all(np.abs(r["rel_err"]) <= 0.01)
+    assert np.all(r["runs"] >= 2)                  # each first try missed by > 1 %
+
+
+def test_targets_outside_the_network_go_straight_to_the_fallback(runs_log):
+    t, tau, s, k = targets()
+    net = FakeNet(nan_mask=np.array([False, True, False, False]))
+    r = surrogate.tune_kappa(None, net, t, tau, s, tol=0.02)
+    assert runs_log[0] == 3                       # the NaN target was not run at NaN
+    assert r["runs"][1] >= 2 and np.all(r["runs"][[0, 2, 3]] == 1)
+    assert np.all(np.abs(r["rel_err"]) <= 0.02)
+
+
+def test_failed_runs_stay_failed_and_are_reported(monkeypatch):
+    def failing(lbm, t, kappa, tau, **kw):
+        return np.full(len(t), np.nan)
+
+    monkeypatch.setattr(surrogate, "sweep_points", failing)
+    t, tau, s, k = targets()
+    r = surrogate.tune_kappa(None, FakeNet(), t, tau, s, tol=0.02, max_rounds=2)
+    assert np.all(np.isnan(r["sigma"])) and np.all(np.isnan(r["rel_err"]))
