@@ -218,7 +218,9 @@ lb_status lb_reduce(lb_ctx *ctx, double out[4]);
  * call before any stream capture. All calls share the array: calls that overlap on the
  * GPU (for example on two streams) race and must be serialised by the caller.
  * Errors: as lb_reduce (LB_EDOMAIN, LB_ENONFINITE poison the context), LB_ECUDA, and
- * LB_EINVAL for an LB_BF16 context (use lb_reduce). */
+ * LB_EINVAL for an LB_BF16 or LB_BC_OPEN context (use lb_reduce). Errors that kernels queued
+ * before this call recorded in the context (LB_ETIMEOUT, LB_EDOMAIN) are returned and poison
+ * the context exactly as in lb_reduce. */
 lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]);
 
 /* Laplace-law measurement of a droplet centred at ((nx-1)/2, (ny-1)/2) (Sec. V.A), on the

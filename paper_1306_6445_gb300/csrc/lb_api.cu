@@ -331,6 +331,11 @@ lb_status ctx_fail(lb_ctx *c, lb_status s, const char *msg, bool poison_ctx) {
     return s;
 }
 
+lb_status ctx_sync_check(lb_ctx *c) {
+    if (!c) return LB_EINVAL;
+    return sync_and_check(c);
+}
+
 }  // namespace lbm
 
 extern "C" {

@@ -179,6 +179,10 @@ struct CtxView {
 lb_status ctx_view(const lb_ctx *c, CtxView *v);
 // record a message; with poison = true also make `s` the context's sticky status
 lb_status ctx_fail(lb_ctx *c, lb_status s, const char *msg, bool poison);
+// wait for the context's stream and fold the device error bits that its kernels set
+// (ERR_TIMEOUT, ERR_DOMAIN) into its sticky status, exactly as every synchronising entry
+// point of lb_api.cu does; allocates nothing
+lb_status ctx_sync_check(lb_ctx *c);
 
 // ---- host thermodynamics (lb_thermo.cpp) ---------------------------------------------
 double p_eos_host(const lb_eos &e, double G, double rho);

@@ -269,8 +269,12 @@ extern "C" lb_status lb_reduce_noalloc(lb_ctx *ctx, double out[4]) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(res, scratch + NA_OUT, 5 * sizeof(double), cudaMemcpyDeviceToHost,
                             v.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(v.stream);
     if (e != cudaSuccess) return lbm::ctx_fail(ctx, LB_ECUDA, cudaGetErrorString(e), false);
+    // wait, then take the context's own error word as lb_reduce does: a bounded wait that
+    // gave up (LB_ETIMEOUT) or a psi-domain violation in a step queued before this call
+    // (LB_EDOMAIN) poisons the context and is returned instead of the sums
+    const lb_status s = lbm::ctx_sync_check(ctx);
+    if (s != LB_OK) return s;
     unsigned long long flags;
     static_assert(sizeof(flags) == sizeof(double), "error word layout");
     std::memcpy(&flags, &res[4], sizeof flags);

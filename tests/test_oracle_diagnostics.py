@@ -53,3 +53,65 @@ def test_interface_height_of_a_tanh_layer_is_the_layer_height():
     for h, tol in ((10.0, 1e-12), (10.5, 1e-12), (10.25, 1e-2), (10.9, 1e-2)):
         col = mid - 0.5 * (0.3 - 0.02) * np.tanh(2.0 * (y - h) / 4.0)
         assert D.interface_height(col, mid) == pytest.approx(h, abs=tol)
+
+
+# ---- laplace_fit: the Fig. 3 reading (Sec. V.A), dp = theta / R + c over several radii ----
+
+RADII = np.array([20.0, 25.0, 30.0, 35.0, 40.0])   # the radii of the paper's Laplace test
+
+
+def test_laplace_fit_recovers_an_exact_line():
+    # theta and c of different sizes and signs, so that a swapped column, a dropped
+    # intercept or a sign slip cannot reproduce both
+    theta, c = 0.8160, -3.0e-4          # Table 3's surface tension at 1 - kappa = 0.5
+    dps = theta / RADII + c
+    got_t, got_c = D.laplace_fit(dps, RADII)
+    assert got_t == pytest.approx(theta, rel=1e-12)
+    assert got_c == pytest.approx(c, rel=1e-9)
+
+
+def test_laplace_fit_through_two_points_is_the_secant():
+    # with two radii the least-squares line passes through both points
+    r = np.array([20.0, 40.0])
+    dps = np.array([0.05, 0.02])
+    t, c = D.laplace_fit(dps, r)
+    slope = (dps[0] - dps[1]) / (1.0 / r[0] - 1.0 / r[1])
+    assert t == pytest.approx(slope, rel=1e-13)
+    assert c == pytest.approx(dps[1] - slope / r[1], rel=1e-12)
+    assert t == pytest.approx(1.2, rel=1e-12) and c == pytest.approx(-0.01, rel=1e-10)
+
+
+def test_laplace_fit_of_noisy_data_is_the_textbook_regression():
+    # simple linear regression of y on x = 1/R: slope = S_xy / S_xx and intercept
+    # = mean(y) - slope mean(x); the residuals are orthogonal to both columns
+    rng = np.random.default_rng(1306)
+    dps = 9.449 / RADII + rng.normal(0.0, 2e-3, RADII.size)
+    t, c = D.laplace_fit(dps, RADII)
+    x = 1.0 / RADII
+    sxy = np.sum((x - x.mean()) * (dps - dps.mean()))
+    sxx = np.sum((x - x.mean()) ** 2)
+    assert t == pytest.approx(sxy / sxx, rel=1e-10)
+    assert c == pytest.approx(dps.mean() - (sxy / sxx) * x.mean(), abs=1e-12)
+    res = dps - (t * x + c)
+    assert abs(np.sum(res)) < 1e-13 and abs(np.sum(res * x)) < 1e-14
+
+
+def test_laplace_fit_of_step_droplets_has_no_slope():
+    # sharp (step) droplets of the oracle's Laplace reading: the pressure jump is the
+    # bulk difference p_EOS(rho_l) - p_EOS(rho_v) at every radius, so the fit returns a
+    # zero surface tension and that difference as its intercept
+    eos = E.cs_eos(0.8)
+    p = L.Params(eos=eos, G=-1.0, kappa=0.0, rates=L.Rates.from_viscosity(0.1))
+    rho_l, rho_v = 0.30, 0.02
+    n = 160
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r = np.hypot(x - (n - 1) / 2, y - (n - 1) / 2)
+    dps, radii = [], []
+    for R in RADII:
+        d = D.laplace(np.where(r < R, rho_l, rho_v), p)
+        dps.append(d["dp"])
+        radii.append(d["R"])
+    t, c = D.laplace_fit(dps, radii)
+    jump = float(E.p_eos(rho_l, eos, -1.0) - E.p_eos(rho_v, eos, -1.0))
+    assert abs(t) < 1e-12 * abs(jump) * 40
+    assert c == pytest.approx(jump, rel=1e-12)
