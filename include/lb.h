@@ -123,8 +123,11 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
                      double sigma_force, const lb_rates *rates, int prec, int bc, void *stream,
                      void *f_a, void *f_b);
 
-/* Number of compiled variants of the step kernel (strip width x shared-memory ring depth
- * x row groups sharing one ring). */
+/* Number of compiled variants of the step kernel: strip width x shared-memory ring depth
+ * x ring kind. Variants 0-3 stage whole stored rows of the strip (all nine populations,
+ * three rows in use at a time); variants 4-6 stage, per psi row, exactly the three plane
+ * groups that row is pulled from (one stage in use at a time, so more CTAs fit on an SM).
+ * Every variant gives identical results. */
 int lb_launch_variants(void);
 
 /* Density-dependent viscosity of Sec. V.C (LB_BC_OPEN contexts): sites with rho < rho_1

@@ -173,15 +173,17 @@ EncodeTiledFn encode_fn() {
 }
 
 // 3-D map over one population buffer: (padded column, row, population); one box is a
-// full lattice row of the strip plus its apron: (tx + ghost + 4) x 1 x 9 (the left apron is
-// as wide as the ghost offset, so a box starts at the strip's own first element).
+// lattice row of the strip plus its apron, (tx + ghost + 4) x 1 x planes: all nine
+// populations for the whole-row ring, one for the stage ring (the left apron is as wide as
+// the ghost offset, so a box starts at the strip's own first element).
 lb_status encode_map(lb_ctx *c, void *buffer, CUtensorMap *map) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(c, LB_ECUDA, "cuTensorMapEncodeTiled unavailable");
     const Geom &g = c->geom;
     const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, 9};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * c->elem, (cuuint64_t)g.plane * c->elem};
-    const cuuint32_t box[3] = {(cuuint32_t)(c->launch.tx + lbm::ghost_of_prec(c->prec) + 4), 1, 9};
+    const cuuint32_t box[3] = {(cuuint32_t)(c->launch.tx + lbm::ghost_of_prec(c->prec) + 4), 1,
+                               (cuuint32_t)lbm::step_variant_planes(c->launch.variant)};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = c->prec == LB_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : c->prec == LB_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16

@@ -159,7 +159,8 @@ lb_status apply_batch_launch(lb_batch *b, int variant, int rows) {
         const lbm::Geom &g = b->geom[i];
         const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.ny, 9};
         const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * b->elem, (cuuint64_t)g.plane * b->elem};
-        const cuuint32_t box[3] = {(cuuint32_t)(tx + lbm::ghost_of_prec(b->prec) + 4), 1, 9};
+        const cuuint32_t box[3] = {(cuuint32_t)(tx + lbm::ghost_of_prec(b->prec) + 4), 1,
+                                   (cuuint32_t)lbm::step_variant_planes(variant)};
         const cuuint32_t estr[3] = {1, 1, 1};
         for (int w = 0; w < 2; ++w) {
             CUresult r = enc(&maps[2 * i + w], dt, 3, buf(b, i, w), dims, strides, box, estr,

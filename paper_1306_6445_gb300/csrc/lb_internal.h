@@ -25,6 +25,15 @@ struct NvtxRange {
 // Error bits written by kernels into the context's device flag word.
 enum : int { ERR_DOMAIN = 1, ERR_TIMEOUT = 2 };
 
+// Order of the population planes in a stored state buffer: grouped by the row each
+// population is pulled from in a step (f_a(x, y) = g_a(x - e_a)): the planes of 2, 5, 6
+// (pulled from row y - 1), then 0, 1, 3 (row y), then 4, 7, 8 (row y + 1). Population a of
+// the state lives in plane plane_of(a); host arrays keep the natural order 0..8.
+__host__ __device__ constexpr int plane_of(int a) {
+    return a == 2 ? 0 : a == 5 ? 1 : a == 6 ? 2 : a == 0 ? 3 : a == 1 ? 4 : a == 3 ? 5
+         : a == 4 ? 6 : a;
+}
+
 // Elements in front of column 0 of every stored row (the last two hold periodic images or
 // edge copies). FP32 uses 8, so that column 0 sits 32 bytes into the row and each warp's
 // 64-column store covers whole 32-byte sectors; the TMA box (columns x0 - 4 ..) then starts
@@ -78,6 +87,7 @@ struct StepLaunch {
 // ---- kernels (lb_kernels.cu) -------------------------------------------------------
 int step_variant_count();
 int step_variant_tx(int variant);
+int step_variant_planes(int variant);   // population planes per TMA box (9 or 3)
 StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
                             int rows_override);
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l);

@@ -52,7 +52,7 @@ __global__ void k_unstream(const T *__restrict__ f, T *__restrict__ g, int nx, i
             tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
             v = f[f_index<T, PACKED>(b, tx, ty, nx, ny, pitch, plane)];
         }
-        T *rowg = g + b * plane + (long long)y * pitch;
+        T *rowg = g + plane_of(b) * plane + (long long)y * pitch;
         rowg[x + GH<T>] = v;
         if (BC == 2) {
             if (x == 0) rowg[GH<T> - 1] = rowg[GH<T> - 2] = v;
@@ -381,12 +381,16 @@ k_reduce_final(const double *__restrict__ partials, int nblocks, double *__restr
 }  // namespace
 
 
-int step_variant_count() { return 4; }
+// the variants of LB_STEP_VARIANTS (lb_step.cuh): strip width and planes per TMA box (9:
+// whole stored rows, 3: one plane group of the stage ring)
+int step_variant_count() { return 7; }
 
 int step_variant_tx(int variant) {
-    static const int tx[] = {128, 128, 240, 64};
-    return (variant >= 0 && variant < 4) ? tx[variant] : 0;
+    static const int tx[] = {128, 128, 240, 64, 128, 128, 240};
+    return (variant >= 0 && variant < 7) ? tx[variant] : 0;
 }
+
+int step_variant_planes(int variant) { return variant >= 4 ? 3 : 9; }
 
 StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
                             int rows_override) {

@@ -54,11 +54,12 @@ template <typename T, bool WALLS>
 __device__ __forceinline__ T na_pull(const T *__restrict__ g, int a, int x, int y, int nx, int ny,
                                      int pitch, long long plane) {
     int sy = y - na_ey(a);
-    if (WALLS && (sy < 0 || sy >= ny)) return g[na_opp(a) * plane + (long long)y * pitch + x + GHOST<T>];
+    if (WALLS && (sy < 0 || sy >= ny))
+        return g[lbm::plane_of(na_opp(a)) * plane + (long long)y * pitch + x + GHOST<T>];
     if (!WALLS) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
     int sx = x - na_ex(a);
     sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-    return g[a * plane + (long long)sy * pitch + sx + GHOST<T>];
+    return g[lbm::plane_of(a) * plane + (long long)sy * pitch + sx + GHOST<T>];
 }
 
 template <typename T, bool WALLS>

@@ -163,13 +163,13 @@ __device__ __forceinline__ T pull_global(const T *__restrict__ g, int a, int x, 
     const int ex = EXv(a), ey = EYv(a);
     int sy = y - ey;
     if ((BC != 0 && sy < 0) || (BC == 1 && sy >= ny))
-        return g[opp(a) * plane + (long long)y * pitch + x + GH<T>];
+        return g[plane_of(opp(a)) * plane + (long long)y * pitch + x + GH<T>];
     if (BC == 0) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
     if (BC == 2) sy = sy >= ny ? ny - 1 : sy;
     int sx = x - ex;
     if (BC == 2) sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
     else sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-    return g[a * plane + (long long)sy * pitch + sx + GH<T>];
+    return g[plane_of(a) * plane + (long long)sy * pitch + sx + GH<T>];
 }
 
 // the value of f_a(x, y) (decoded from the storage type)
@@ -210,6 +210,15 @@ __host__ __device__ constexpr size_t step_smem_bytes() {
     return step_bar_offset<T, TX, S, G>() + (size_t)S * 8 + 128;   // + room to align the base
 }
 
+// resident CTAs per SM a step kernel is compiled for (its __launch_bounds__ minimum): as
+// many as its shared memory allows (with the 1 KB the hardware reserves per CTA, out of
+// 228 KB), but no more than leave each thread 88 registers
+__host__ __device__ constexpr int resident_ctas(size_t smem, int threads) {
+    const int by_smem = (int)((228u * 1024u) / (smem + 1024u));
+    const int by_regs = 65536 / (threads * 88);
+    return by_smem < by_regs ? by_smem : by_regs;
+}
+
 template <typename T>
 struct Vec2Of;
 template <>
@@ -246,10 +255,11 @@ template <typename T, int BC, int BW, bool ADJ>
 __device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, int cA, int cB,
                                       bool bottom, bool top, const DevConsts<Arith<T>> &P) {
     using A = Arith<T>;
+    // stored population a sits in ring plane plane_of(a)
     auto two = [&](const T *row, int a, int dc) -> V2<A> {
-        if (ADJ && dc == 0) return ring_pair<T>(row + a * BW + cA, a, P);
-        return V2<A>(pop_dec<T>(row[a * BW + cA + dc], a, P),
-                     pop_dec<T>(row[a * BW + cB + dc], a, P));
+        const T *pl = row + plane_of(a) * BW;
+        if (ADJ && dc == 0) return ring_pair<T>(pl + cA, a, P);
+        return V2<A>(pop_dec<T>(pl[cA + dc], a, P), pop_dec<T>(pl[cB + dc], a, P));
     };
     f[0] = two(r.z, 0, 0);
     f[1] = two(r.z, 1, -1);
@@ -482,7 +492,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH<T>);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
-                store_pop_pair<T>(gout + (idx + a * plane), fc[a], both, a, P);
+                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
             if (BC == 2) {
                 // open sides: the ghost columns repeat the edge columns (zero gradient)
                 if (x == 0 || x + 1 >= nx - 1) {
@@ -490,7 +500,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
                         const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
-                        T *rb = gout + (rowi + a * plane);
+                        T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
                         if (both && x + 1 == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v1;
@@ -502,7 +512,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
-                    T *rb = gout + (rowi + a * plane);
+                    T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
                     if (x >= nx - 2) rb[x - nx + GH<T>] = v0;
@@ -533,6 +543,280 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
     return 0;
 }
 
+// ---------------------------------------------------------------- stage ring
+
+// Every stored value of the state is pulled exactly once per step: population a of stored
+// row R feeds psi row R + e_a,y. The planes are stored in three groups of three by that
+// row offset (plane_of): group 0 = populations 2, 5, 6 (pulled from the row below),
+// group 1 = 0, 1, 3 (the same row), group 2 = 4, 7, 8 (the row above). Stage i of this
+// ring holds exactly what psi row P_i consumes: group 0 of row P_i - 1, group 1 of row
+// P_i and group 2 of row P_i + 1, fetched by three TMA loads of 3 planes each. At a wall
+// the bounced-back group comes from row P_i itself with the opposite populations (group 2
+// for group 0 at the bottom, group 0 for group 2 at the top; the positions inside the
+// groups are opposite populations), and at an open top group 2 comes from row ny - 1.
+// A stage is read by one iteration only, so one stage is in use while S - 1 are in flight.
+
+// elements between the starts of two groups of a stage: a TMA destination must start on
+// a 128-byte boundary
+template <typename T, int TX>
+__host__ __device__ constexpr int group_elems() {
+    return (int)(((3u * ring_width<T, TX>() * sizeof(T) + 127u) / 128u) * 128u / sizeof(T));
+}
+
+template <typename T, int TX, int S>
+__host__ __device__ constexpr size_t stage_bar_offset() {
+    return (size_t)S * 3u * group_elems<T, TX>() * sizeof(T) +
+           (((size_t)4 * (TX + 4) * sizeof(Arith<T>) + 15u) / 16u * 16u);
+}
+template <typename T, int TX, int S>
+__host__ __device__ constexpr size_t stage_smem_bytes() {
+    return stage_bar_offset<T, TX, S>() + (size_t)S * 8 + 128;
+}
+template <typename T, int TX, int S>
+__host__ __device__ constexpr int stage_min_blocks() {
+    return resident_ctas(stage_smem_bytes<T, TX, S>(), TX / 2);
+}
+
+// f of two sites at stage columns cA, cB (see pull2); population a sits at group
+// plane_of(a) / 3, place plane_of(a) % 3 of the stage; only the column offset depends on
+// the boundary (0 for a bounced-back link)
+template <typename T, int BC, int BW, int GS, bool ADJ>
+__device__ __forceinline__ void pull_stage(V2<Arith<T>> (&f)[9], const T *stg, int cA, int cB,
+                                           bool bottom, bool top, const DevConsts<Arith<T>> &P) {
+    using A = Arith<T>;
+    auto two = [&](int a, int dc) -> V2<A> {
+        const T *pl = stg + (plane_of(a) / 3) * GS + (plane_of(a) % 3) * BW;
+        if (ADJ && dc == 0) return ring_pair<T>(pl + cA, a, P);
+        return V2<A>(pop_dec<T>(pl[cA + dc], a, P), pop_dec<T>(pl[cB + dc], a, P));
+    };
+    f[0] = two(0, 0);
+    f[1] = two(1, -1);
+    f[3] = two(3, 1);
+    f[2] = two(2, 0);
+    f[4] = two(4, 0);
+    if (BC != 0 && bottom) {
+        f[5] = two(5, 0);
+        f[6] = two(6, 0);
+    } else {
+        f[5] = two(5, -1);
+        f[6] = two(6, 1);
+    }
+    if (BC == 1 && top) {
+        f[7] = two(7, 0);
+        f[8] = two(8, 0);
+    } else {
+        f[7] = two(7, 1);
+        f[8] = two(8, -1);
+    }
+}
+
+// One time step for one strip with the stage ring: the same work, order and arithmetic as
+// march (identical results), for columns x0 .. x0+w-1 and rows yb .. yb+n-1 visited from
+// `start` in direction dir. Psi row P_i = start + (i - 1) dir, i = 0 .. n + 1, is formed
+// from stage i (slot i mod S). Iteration k waits for stage k + 2, forms psi of row
+// P_{k+2} (keeping its populations for the next collision), passes a barrier, lets thread
+// 0 request stages up to k + 2 + S into the freed slots, then collides row start + k dir.
+template <typename T, int EOS, int BC, int TX, int S>
+__device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restrict__ gout,
+                                           const DevConsts<Arith<T>> &P, const int nx,
+                                           const int ny, const int pitch, const unsigned plane,
+                                           const int x0, const int w, const int yb, const int n,
+                                           const int dir, unsigned char *smem_raw, bool &bad) {
+    constexpr bool WALLS = BC != 0;
+    static_assert(S >= 2, "one stage in use and at least one in flight");
+    static_assert(TX % 4 == 0 && ring_width<T, TX>() <= 256,
+                  "TMA box: 16-byte aligned start, at most 256 columns");
+    constexpr int NT = TX / 2;
+    constexpr int L = AL<T>;
+    constexpr int BW = ring_width<T, TX>();
+    constexpr int RW = TX + 4;
+    constexpr int PR = 4;           // psi ring rows
+    constexpr int GS = group_elems<T, TX>();
+    constexpr int STAGE_ELEMS = 3 * GS;
+    constexpr uint32_t STAGE_BYTES = 9u * BW * sizeof(T);
+    using A = Arith<T>;
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    A *psis = reinterpret_cast<A *>(ring + S * STAGE_ELEMS);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + stage_bar_offset<T, TX, S>());
+
+    const int t = (int)threadIdx.x;
+    const bool lead = t == 0;             // requests the stages
+    const int c0 = 2 * t;
+    const bool act = c0 < w;
+    const bool both = c0 + 1 < w;
+    const int start = dir > 0 ? yb : yb + n - 1;
+    const int ns = n + 2;                 // stages
+
+    // the lead thread requests stages in order
+    int ji = 0, si = 0;
+    auto issue_upto = [&](int jmax) {
+        for (; ji <= jmax && ji < ns; ++ji) {
+            const int Y = start + (ji - 1) * dir;
+            const uint32_t sl = (uint32_t)si;
+            si = (si + 1 == S) ? 0 : si + 1;
+            if (Y == P.stall_row) continue;   // test hook: the wait for this stage must time out
+            int r0 = Y - 1, r1 = Y, r2 = Y + 1, p0 = 0, p2 = 6;
+            if (BC == 0) {
+                r0 = r0 < 0 ? r0 + ny : (r0 >= ny ? r0 - ny : r0);
+                r1 = r1 < 0 ? r1 + ny : (r1 >= ny ? r1 - ny : r1);
+                r2 = r2 < 0 ? r2 + ny : (r2 >= ny ? r2 - ny : r2);
+            } else if (Y >= 0 && Y < ny) {
+                // a psi row outside the lattice is never formed: its rows outside the lattice
+                // are filled with zeros by the TMA unit
+                if (Y == 0) { r0 = 0; p0 = 6; }                 // bounce-back below row 0
+                if (Y == ny - 1) { r2 = ny - 1; p2 = BC == 1 ? 0 : 6; }   // wall / open top
+            }
+            T *dst = ring + sl * STAGE_ELEMS;
+            mbar_arrive_expect_tx(&bar[sl], STAGE_BYTES);
+            // element x0 holds column x0 - L, the first of the box
+            tma_load_3d(dst, tmap, x0, r0, p0, &bar[sl]);
+            tma_load_3d(dst + GS, tmap, x0, r1, 3, &bar[sl]);
+            tma_load_3d(dst + 2 * GS, tmap, x0, r2, p2, &bar[sl]);
+        }
+    };
+    if (lead) issue_upto(S - 1);
+
+    // slot and phase parity of the stage awaited next (every thread tracks them)
+    int ws = 0;
+    uint32_t wpar = 0;
+    auto wait_next = [&]() -> bool {
+        const bool ok = mbar_wait_bounded(&bar[ws], wpar);
+        if (++ws == S) { ws = 0; wpar ^= 1u; }
+        return ok;
+    };
+    auto stage_of = [&](int j) -> const T * { return ring + (j % S) * STAGE_ELEMS; };
+
+    auto psi_row = [&](int Y, const T *stg, V2<A> (&keep)[9]) {
+        if (WALLS && (Y < 0 || Y >= ny)) return;
+        A *ps = psis + (Y & (PR - 1)) * RW;
+        const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
+        if (act) {
+            pull_stage<T, BC, BW, GS, true>(keep, stg, c0 + L, c0 + L + 1, bottom, top, P);
+            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
+            if (both) {
+                store_pair<A>(ps + c0 + 2, psi, true);
+            } else {
+                ps[c0 + 2] = psi.lo();
+            }
+        }
+        if (t == NT - 1) {   // the two halo columns x0-1 and x0+w as one packed pair
+            V2<A> h[9];
+            int ha = L - 1, hb = w + L;
+            if (BC == 2) {   // open sides: psi beyond the lattice is that of its edge column
+                if (x0 == 0) ha = L;
+                if (x0 + w == nx) hb = w + L - 1;
+            }
+            pull_stage<T, BC, BW, GS, false>(h, stg, ha, hb, bottom, top, P);
+            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
+            ps[1] = psi.lo();
+            ps[w + 2] = psi.hi();
+        }
+    };
+    auto psi_at = [&](int Y) -> const A * {
+        if (WALLS) Y = Y < 0 ? 0 : (Y >= ny ? ny - 1 : Y);
+        return psis + (Y & (PR - 1)) * RW;
+    };
+
+    // prologue: psi of rows start - dir (stage 0) and start (stage 1, populations kept)
+    bool tmo = false;
+    int jw = 0;                           // first stage not yet seen complete
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+        tmo |= !wait_next();
+        if (!tmo) jw = j + 1;
+    }
+    V2<A> fA[9], fB[9];
+    if (!tmo) {
+        psi_row(start - dir, stage_of(0), fB);
+        psi_row(start, stage_of(1), fA);
+    }
+    tmo = __syncthreads_or(tmo);
+    if (!tmo && lead) issue_upto(S + 1);
+
+    auto body = [&](int k, V2<A> (&fc)[9], V2<A> (&fn)[9]) -> bool {
+        const int y = start + k * dir;
+        const int j = k + 2;
+        const T *stg = ring + ws * STAGE_ELEMS;   // stage j sits in slot j mod S
+        if (!tmo) tmo = !wait_next();
+        if (!tmo) jw = j + 1;
+        if (!tmo) psi_row(y + dir, stg, fn);
+        if (__syncthreads_or(tmo)) return false;
+        if (lead) issue_upto(j + S);      // refill the slot of stage j and the earlier ones
+
+        if (act) {
+            const A *pm = psi_at(y - 1);
+            const A *p0 = psi_at(y);
+            const A *pp = psi_at(y + 1);
+            const int c = c0 + 2;
+            const V2<A> m0 = lds_pair<A>(pm + c), z0 = lds_pair<A>(p0 + c), q0 = lds_pair<A>(pp + c);
+            const A mL = pm[c - 1], mR = pm[c + 2], zL = p0[c - 1], zR = p0[c + 2];
+            const A qL = pp[c - 1], qR = pp[c + 2];
+            V2<A> pn[9];
+            pn[0] = z0;
+            pn[1] = V2<A>(z0.hi(), zR);
+            pn[2] = q0;
+            pn[3] = V2<A>(zL, z0.lo());
+            pn[4] = m0;
+            pn[5] = V2<A>(q0.hi(), qR);
+            pn[6] = V2<A>(qL, q0.lo());
+            pn[7] = V2<A>(mL, m0.lo());
+            pn[8] = V2<A>(m0.hi(), mR);
+            collide_pair<A, BC == 2>(fc, pn, P);
+
+            const int x = x0 + c0;
+            const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH<T>);
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
+            if (BC == 2) {
+                if (x == 0 || x + 1 >= nx - 1) {
+                    const unsigned rowi = (unsigned)y * (unsigned)pitch;
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) {
+                        const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                        T *rb = gout + (rowi + plane_of(a) * plane);
+                        if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
+                        if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
+                        if (both && x + 1 == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v1;
+                    }
+                }
+            } else if (x < 2 || x + 1 >= nx - 2) {
+                const unsigned rowi = (unsigned)y * (unsigned)pitch;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                    T *rb = gout + (rowi + plane_of(a) * plane);
+                    if (x < 2) rb[nx + GH<T> + x] = v0;
+                    if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
+                    if (x >= nx - 2) rb[x - nx + GH<T>] = v0;
+                    if (both && x + 1 >= nx - 2) rb[x + 1 - nx + GH<T>] = v1;
+                }
+            }
+        }
+        return true;
+    };
+
+    int k = 0;
+    bool ok = !tmo;
+    if (ok) {
+        for (; k + 1 < n; k += 2) {
+            if (!body(k, fA, fB) || !body(k + 1, fB, fA)) { ok = false; break; }
+        }
+        if (ok && k < n) ok = body(k, fA, fB);
+    }
+    if (!ok) {
+        // a bounded wait gave up: let every requested stage land (each wait bounded; the
+        // test hook's stage was never requested), then leave
+        if (lead)
+            for (int j = jw; j < ji; ++j)
+                if (start + (j - 1) * dir != P.stall_row)
+                    (void)mbar_wait_bounded(&bar[j % S], (uint32_t)((j / S) & 1));
+        __syncthreads();
+        return ERR_TIMEOUT;
+    }
+    return 0;
+}
+
 __device__ __forceinline__ unsigned char *align_smem128(unsigned char *p) {
     return p + ((128u - (smem_u32(p) & 127u)) & 127u);
 }
@@ -551,7 +835,7 @@ __device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
 
 // Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
 template <typename T, int EOS, int BC, int TX, int S, int G>
-__global__ void __launch_bounds__(G * TX / 2)
+__global__ void __launch_bounds__(G * TX / 2, resident_ctas(step_smem_bytes<T, TX, S, G>(), G * TX / 2))
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
                const unsigned plane, const int rows, const int order, int *__restrict__ err) {
@@ -616,23 +900,92 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
     }
 }
 
+// Single lattice with the stage ring (same grid, parameters and results as k_pull_collide).
+template <typename T, int EOS, int BC, int TX, int S>
+__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>())
+k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
+                     const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
+                     const unsigned plane, const int rows, const int order, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    if (threadIdx.x == 0) prefetch_tensormap(&tin);
+    init_ring_barriers<S>(reinterpret_cast<uint64_t *>(smem_raw + stage_bar_offset<T, TX, S>()),
+                          false);
+    grid_dependency_wait();
+    grid_dependents_launch();
+    const int bx = order ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int by = order ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int x0 = bx * TX;
+    const int yb = by * rows;
+    bool bad = false;
+    const int st = march_stage<T, EOS, BC, TX, S>(&tin, gout, P, nx, ny, pitch, plane, x0,
+                                                  min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
+                                                  ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
+    if (threadIdx.x == 0 && st) atomicOr(err, st);
+    if (bad) atomicOr(err, ERR_DOMAIN);
+}
+
+// Many lattices with the stage ring (as k_batch_step).
+template <typename T, int EOS, int TX, int S>
+__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>())
+k_batch_step_stage(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
+                   const BatchItem *__restrict__ items, const int n_items, const int phase,
+                   int *__restrict__ errs) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = align_smem128(smem_dyn);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + stage_bar_offset<T, TX, S>());
+    init_ring_barriers<S>(bar, false);
+    grid_dependency_wait();
+    grid_dependents_launch();
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const BatchItem it = items[phase ? n_items - 1 - i : i];
+        const BatchLattice<T> &L = lats[it.lat];
+        const DevConsts<Arith<T>> P = L.P;
+        const CUtensorMap *map = maps + 2 * it.lat + phase;
+        if (threadIdx.x == 0) prefetch_tensormap(map);
+        bool bad = false;
+        const int st = march_stage<T, EOS, 0, TX, S>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
+                                                     L.plane, it.x0, it.w, it.yb, it.n,
+                                                     phase ? -it.dir : it.dir, smem_raw, bad);
+        if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
+        if (st) {
+            if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
+            return;
+        }
+        __syncthreads();
+        init_ring_barriers<S>(bar, true);
+    }
+}
+
 // ---------------------------------------------------------------- dispatch
 
 
 
 
-template <typename T, int EOS, int BC, int TX, int S, int G>
+// K: ring kind, 0 = whole stored rows (k_pull_collide), 1 = stages (k_pull_collide_stage)
+template <typename T, int EOS, int BC, int TX, int S, int K>
+constexpr auto step_kernel() {
+    if constexpr (K == 0) return k_pull_collide<T, EOS, BC, TX, S, 1>;
+    else return k_pull_collide_stage<T, EOS, BC, TX, S>;
+}
+template <typename T, int TX, int S, int K>
+constexpr size_t step_kernel_smem() {
+    if constexpr (K == 0) return step_smem_bytes<T, TX, S, 1>();
+    else return stage_smem_bytes<T, TX, S>();
+}
+
+template <typename T, int EOS, int BC, int TX, int S, int K>
 cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
                          const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                          bool configure) {
-    auto kern = k_pull_collide<T, EOS, BC, TX, S, G>;
-    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    auto kern = step_kernel<T, EOS, BC, TX, S, K>();
+    constexpr size_t smem = step_kernel_smem<T, TX, S, K>();
     if (configure) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
-    cfg.blockDim = dim3(G * TX / 2);
+    cfg.blockDim = dim3(TX / 2);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     // programmatic dependent launch: this grid's CTAs may start their set-up while the
@@ -646,99 +999,116 @@ cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
                               g.pitch, (unsigned)g.plane, rows, order, err);
 }
 
-template <typename T, int EOS, int TX, int S, int G>
+template <typename T, int EOS, int TX, int S, int K>
 cudaError_t step_bc(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
                     void *out, int *err, cudaStream_t st, bool configure) {
     switch (g.walls) {
-        case 0: return step_variant<T, EOS, 0, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
-        case 1: return step_variant<T, EOS, 1, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case 0: return step_variant<T, EOS, 0, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
+        case 1: return step_variant<T, EOS, 1, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
         default:
             // open boundaries (and nu(rho)) are compiled for FP32 and FP64 only
             if constexpr (std::is_same<T, __nv_bfloat16>::value) return cudaErrorInvalidValue;
-            else return step_variant<T, EOS, 2, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+            else return step_variant<T, EOS, 2, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
     }
 }
 
-template <typename T, int TX, int S, int G>
+template <typename T, int TX, int S, int K>
 cudaError_t step_eos(const Consts &c, const Geom &g, int rows, int order, const CUtensorMap &tin,
                      void *out, int *err, cudaStream_t st, bool configure) {
     switch (c.eos_kind) {
-        case LB_EOS_CS: return step_bc<T, LB_EOS_CS, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
-        case LB_EOS_EXP: return step_bc<T, LB_EOS_EXP, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
-        default: return step_bc<T, LB_EOS_PIECEWISE, TX, S, G>(c, g, rows, order, tin, out, err, st, configure);
+        case LB_EOS_CS: return step_bc<T, LB_EOS_CS, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
+        case LB_EOS_EXP: return step_bc<T, LB_EOS_EXP, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
+        default: return step_bc<T, LB_EOS_PIECEWISE, TX, S, K>(c, g, rows, order, tin, out, err, st, configure);
     }
 }
+
+// The compiled launch variants: (strip width TX, ring depth S, ring kind K). The table is
+// mirrored by step_variant_tx / step_variant_planes (lb_kernels.cu).
+#define LB_STEP_VARIANTS(X) \
+    X(0, 128, 5, 0)         \
+    X(1, 128, 6, 0)         \
+    X(2, 240, 5, 0)         \
+    X(3, 64, 6, 0)          \
+    X(4, 128, 3, 1)         \
+    X(5, 128, 4, 1)         \
+    X(6, 240, 3, 1)
 
 template <typename T>
 cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l, int order,
                           const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                           bool configure) {
     switch (l.variant) {
-        case 0: return step_eos<T, 128, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
-        case 1: return step_eos<T, 128, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
-        case 2: return step_eos<T, 240, 5, 1>(c, g, l.rows, order, tin, out, err, st, configure);
-        case 3: return step_eos<T, 64, 6, 1>(c, g, l.rows, order, tin, out, err, st, configure);
+#define LB_X(v, tx, s, k) \
+        case v: return step_eos<T, tx, s, k>(c, g, l.rows, order, tin, out, err, st, configure);
+        LB_STEP_VARIANTS(LB_X)
+#undef LB_X
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int EOS, int BC, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int K>
 int occupancy_variant() {
     int n = 0;
-    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
-    auto kern = k_pull_collide<T, EOS, BC, TX, S, G>;
+    constexpr size_t smem = step_kernel_smem<T, TX, S, K>();
+    auto kern = step_kernel<T, EOS, BC, TX, S, K>();
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, G * TX / 2, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX / 2, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-template <typename T, int EOS, int TX, int S, int G>
+template <typename T, int EOS, int TX, int S, int K>
 int occupancy_bc(int bc) {
     switch (bc) {
-        case 0: return occupancy_variant<T, EOS, 0, TX, S, G>();
-        case 1: return occupancy_variant<T, EOS, 1, TX, S, G>();
+        case 0: return occupancy_variant<T, EOS, 0, TX, S, K>();
+        case 1: return occupancy_variant<T, EOS, 1, TX, S, K>();
         default:
             if constexpr (std::is_same<T, __nv_bfloat16>::value) return 0;
-            else return occupancy_variant<T, EOS, 2, TX, S, G>();
+            else return occupancy_variant<T, EOS, 2, TX, S, K>();
     }
 }
 
-template <typename T, int TX, int S, int G>
+template <typename T, int TX, int S, int K>
 int occupancy_eos(int eos, int bc) {
     switch (eos) {
-        case LB_EOS_CS: return occupancy_bc<T, LB_EOS_CS, TX, S, G>(bc);
-        case LB_EOS_EXP: return occupancy_bc<T, LB_EOS_EXP, TX, S, G>(bc);
-        default: return occupancy_bc<T, LB_EOS_PIECEWISE, TX, S, G>(bc);
+        case LB_EOS_CS: return occupancy_bc<T, LB_EOS_CS, TX, S, K>(bc);
+        case LB_EOS_EXP: return occupancy_bc<T, LB_EOS_EXP, TX, S, K>(bc);
+        default: return occupancy_bc<T, LB_EOS_PIECEWISE, TX, S, K>(bc);
     }
 }
 
 template <typename T>
 int occupancy(int variant, int eos, int w) {
     switch (variant) {
-        case 0: return occupancy_eos<T, 128, 5, 1>(eos, w);
-        case 1: return occupancy_eos<T, 128, 6, 1>(eos, w);
-        case 2: return occupancy_eos<T, 240, 5, 1>(eos, w);
-        case 3: return occupancy_eos<T, 64, 6, 1>(eos, w);
+#define LB_X(v, tx, s, k) \
+        case v: return occupancy_eos<T, tx, s, k>(eos, w);
+        LB_STEP_VARIANTS(LB_X)
+#undef LB_X
         default: return 0;
     }
 }
 
-template <typename T, int EOS, int TX, int S, int G>
+template <typename T, int EOS, int TX, int S, int K>
+constexpr auto batch_kernel() {
+    if constexpr (K == 0) return k_batch_step<T, EOS, TX, S, 1>;
+    else return k_batch_step_stage<T, EOS, TX, S>;
+}
+
+template <typename T, int EOS, int TX, int S, int K>
 cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void *maps,
                           const void *lats, const BatchItem *items, int n_items, int phase,
                           int *errs, cudaStream_t st) {
-    auto kern = k_batch_step<T, EOS, TX, S, G>;
-    constexpr size_t smem = step_smem_bytes<T, TX, S, G>();
+    auto kern = batch_kernel<T, EOS, TX, S, K>();
+    constexpr size_t smem = step_kernel_smem<T, TX, S, K>();
     if (configure) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, G * TX / 2, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, TX / 2, smem);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(G * TX / 2);
+    cfg.blockDim = dim3(TX / 2);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -751,17 +1121,17 @@ cudaError_t batch_variant(bool configure, int *ctas_per_sm, int grid, const void
                               errs);
 }
 
-template <typename T, int TX, int S, int G>
+template <typename T, int TX, int S, int K>
 cudaError_t batch_eos(int eos, bool configure, int *occ, int grid, const void *maps,
                       const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
                       cudaStream_t st) {
     switch (eos) {
         case LB_EOS_CS:
-            return batch_variant<T, LB_EOS_CS, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_CS, TX, S, K>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
         case LB_EOS_EXP:
-            return batch_variant<T, LB_EOS_EXP, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_EXP, TX, S, K>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
         default:
-            return batch_variant<T, LB_EOS_PIECEWISE, TX, S, G>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+            return batch_variant<T, LB_EOS_PIECEWISE, TX, S, K>(configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
     }
 }
 
@@ -770,10 +1140,10 @@ cudaError_t batch_dispatch(int variant, int eos, bool configure, int *occ, int g
                            const void *maps, const void *lats, const BatchItem *items,
                            int n_items, int phase, int *errs, cudaStream_t st) {
     switch (variant) {
-        case 0: return batch_eos<T, 128, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 1: return batch_eos<T, 128, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 2: return batch_eos<T, 240, 5, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
-        case 3: return batch_eos<T, 64, 6, 1>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+#define LB_X(v, tx, s, k) \
+        case v: return batch_eos<T, tx, s, k>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+        LB_STEP_VARIANTS(LB_X)
+#undef LB_X
         default: return cudaErrorInvalidValue;
     }
 }
