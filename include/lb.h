@@ -127,7 +127,7 @@ lb_status lb_init_ex(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, 
  * x ring kind. Variants 0-3 stage whole stored rows of the strip (all nine populations,
  * three rows in use at a time); variants 4-6 stage, per psi row, exactly the three plane
  * groups that row is pulled from (one stage in use at a time, so more CTAs fit on an SM).
- * Every variant gives identical results. */
+ * Every variant gives identical results. Contexts and batches start with variant 4. */
 int lb_launch_variants(void);
 
 /* Density-dependent viscosity of Sec. V.C (LB_BC_OPEN contexts): sites with rho < rho_1
@@ -323,9 +323,13 @@ lb_status lb_batch_get_populations(lb_batch *b, int i, void *dst, size_t bytes);
  * Synchronises. */
 lb_status lb_batch_measure(lb_batch *b, const double *radius, double *out);
 
-/* Time a few steps of every compiled variant and rows-per-item choice on this batch and
- * keep the fastest; it leaves all populations zeroed and the step count at 0, so call it
- * before lb_batch_set_rho_u. Writes the choice if the pointers are not NULL. */
+/* Time a few steps of every compiled variant and rows-per-item choice in {8, 12, 16, 24,
+ * 32} on this batch and keep the fastest. The trial launches take real steps of the
+ * current states (set them first: the cost of a step depends on the state), after the
+ * populations, per-lattice error flags, phase and step count have been saved to a
+ * temporary device buffer the size of the batch's pool; they are restored afterwards, so
+ * the batch is unchanged. Writes the choice if the pointers are not NULL. Synchronises.
+ * Errors: LB_EINVAL, LB_ENOMEM (no room for the copy; nothing changed), LB_ECUDA. */
 lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *rows);
 
 /* Choose the variant and rows per work item directly; report the current launch. */

@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblb_gb300.so")
-SOURCES = ["lb_step_f32.cu", "lb_step_f64.cu", "lb_step_bf16.cu", "lb_batch_kernels.cu",
+SOURCES = ["lb_step_f32.cu", "lb_step_f32_stage.cu", "lb_step_f64.cu", "lb_step_f64_stage.cu",
+           "lb_step_bf16.cu", "lb_step_bf16_stage.cu", "lb_batch_kernels.cu", "lb_batch_stage.cu",
            "lb_kernels.cu", "lb_api.cu", "lb_thermo.cpp", "lb_noalloc.cu", "lb_batch.cu",
            "lb_mlp.cu", "lb_probe.cu"]
 HEADERS = ["lb_internal.h", "lb_device.cuh", "lb_step.cuh"]

@@ -302,7 +302,7 @@ lb_status create(lb_ctx **out, int nx, int ny, const lb_eos *eos, double G, doub
         lb_free(c);
         return LB_ECUDA;
     }
-    if ((s = apply_launch(c, 0, 0)) != LB_OK) {
+    if ((s = apply_launch(c, lbm::default_step_variant(), 0)) != LB_OK) {
         std::fprintf(stderr, "lb_init: %s\n", c->msg.c_str());
         lb_free(c);
         return s;

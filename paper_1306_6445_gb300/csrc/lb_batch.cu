@@ -349,7 +349,7 @@ lb_status lb_batch_create(lb_batch **out, int n, const lb_lattice_desc *descs, i
         return LB_ENOMEM;
     }
     s = prec == LB_FP32 ? upload_lattices<float>(b) : upload_lattices<double>(b);
-    if (s == LB_OK) s = apply_batch_launch(b, 0, 16);
+    if (s == LB_OK) s = apply_batch_launch(b, lbm::default_step_variant(), 16);
     if (s != LB_OK) {
         std::fprintf(stderr, "lb_batch_create: %s\n", b->msg.c_str());
         lb_batch_free(b);
@@ -380,24 +380,44 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *row
     if (!b) return LB_EINVAL;
     if (b->sticky != LB_OK) return b->sticky;
     if (trial_steps < 2) trial_steps = 2;
-    // timed on the current contents of the buffers, which are zeroed afterwards: call it
-    // before setting the lattices' states
-    const int cand_rows[] = {8, 12, 16, 24};
+    // the trial launches take real steps of the current states: the pool, the error flags,
+    // the phase and the step count are saved first and restored afterwards
+    const size_t total = b->off[1].back() +
+                         (lb_buffer_bytes(b->geom.back().nx, b->geom.back().ny, b->prec) + 255) / 256 * 256;
+    void *saved = nullptr;
+    int *saved_errs = nullptr;
+    if (cudaMalloc(&saved, total) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LB_ENOMEM, "lb_batch_autotune: no device memory for the state copy");
+    }
+    if (cudaMalloc(&saved_errs, b->n * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(saved);
+        return bfail(b, LB_ENOMEM, "lb_batch_autotune: no device memory for the state copy");
+    }
+    const int phase0 = b->phase;
+    const long long steps0 = b->steps;
+    const int v0 = b->variant, r0 = b->rows;
+    cudaError_t e = cudaMemcpyAsync(saved, b->pool, total, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(saved_errs, b->d_errs, b->n * sizeof(int), cudaMemcpyDeviceToDevice,
+                            b->stream);
+    const int cand_rows[] = {8, 12, 16, 24, 32};
     float best = 1e30f;
-    int bv = b->variant, br = b->rows;
-    cudaEvent_t e0, e1;
-    LB_BCUDA(b, cudaEventCreate(&e0));
-    LB_BCUDA(b, cudaEventCreate(&e1));
-    for (int v = 0; v < lbm::step_variant_count(); ++v) {
+    int bv = v0, br = r0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int v = 0; v < lbm::step_variant_count() && e == cudaSuccess; ++v) {
         for (int r : cand_rows) {
             if (apply_batch_launch(b, v, r) != LB_OK) continue;
             if (launch_steps(b, 1) != LB_OK) continue;                 // warm-up
             cudaEventRecord(e0, b->stream);
             if (launch_steps(b, trial_steps) != LB_OK) continue;
             cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
+            e = cudaEventSynchronize(e1);
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             if (ms > 0 && ms < best) {
                 best = ms;
                 bv = v;
@@ -405,16 +425,22 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *row
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // put the states back (whatever the trials did)
+    cudaError_t e2 = cudaMemcpyAsync(b->pool, saved, total, cudaMemcpyDeviceToDevice, b->stream);
+    if (e2 == cudaSuccess)
+        e2 = cudaMemcpyAsync(b->d_errs, saved_errs, b->n * sizeof(int), cudaMemcpyDeviceToDevice,
+                             b->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(b->stream);
+    cudaFree(saved);
+    cudaFree(saved_errs);
+    b->phase = phase0;
+    b->steps = steps0;
+    if (e != cudaSuccess) return bfail(b, LB_ECUDA, cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return bfail(b, LB_ECUDA, cudaGetErrorString(e2));
     lb_status s = apply_batch_launch(b, bv, br);
     if (s != LB_OK) return s;
-    size_t total = b->off[1].back() + (lb_buffer_bytes(b->geom.back().nx, b->geom.back().ny, b->prec) + 255) / 256 * 256;
-    LB_BCUDA(b, cudaMemsetAsync(b->pool, 0, total, b->stream));
-    LB_BCUDA(b, cudaMemsetAsync(b->d_errs, 0, b->n * sizeof(int), b->stream));
-    LB_BCUDA(b, cudaStreamSynchronize(b->stream));
-    b->steps = 0;
-    b->phase = 0;
     if (variant) *variant = bv;
     if (rows) *rows = br;
     return LB_OK;

@@ -1,5 +1,6 @@
-// Batched-lattice kernels: the persistent step over work items (FP32, FP64) and the
-// per-lattice Laplace measurement.
+// Batched-lattice kernels: the persistent step over work items with the whole-row ring
+// (FP32, FP64; the stage ring is in lb_batch_stage.cu) and the per-lattice Laplace
+// measurement.
 #include "lb_step.cuh"
 
 namespace lbm {
@@ -74,18 +75,7 @@ cudaError_t launch_batch_measure(int prec, int eos_kind, const void *lats, int n
 }
 
 
-cudaError_t batch_f32(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
-                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
-                      cudaStream_t st) {
-    return batch_dispatch<float>(variant, eos, configure, occ, grid, maps, lats, items, n_items,
-                                 phase, errs, st);
-}
-
-cudaError_t batch_f64(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
-                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
-                      cudaStream_t st) {
-    return batch_dispatch<double>(variant, eos, configure, occ, grid, maps, lats, items, n_items,
-                                  phase, errs, st);
-}
+LB_BATCH_UNIT(f32, float, 0)
+LB_BATCH_UNIT(f64, double, 0)
 
 }  // namespace lbm

@@ -88,31 +88,37 @@ struct StepLaunch {
 int step_variant_count();
 int step_variant_tx(int variant);
 int step_variant_planes(int variant);   // population planes per TMA box (9 or 3)
+int default_step_variant();
 StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
                             int rows_override);
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l);
-// tensor_map_in: a CUtensorMap describing the input buffer (3-D: x, y, population)
-// per-precision step units (lb_step_f32.cu, lb_step_f64.cu, lb_step_bf16.cu); configure:
-// set the kernel attributes only. tensor_map_in points to a CUtensorMap.
-cudaError_t step_f32(const Consts &c, const Geom &g, const StepLaunch &l, int order,
-                     const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
-                     bool configure);
-cudaError_t step_f64(const Consts &c, const Geom &g, const StepLaunch &l, int order,
-                     const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
-                     bool configure);
-cudaError_t step_bf16(const Consts &c, const Geom &g, const StepLaunch &l, int order,
-                      const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
-                      bool configure);
-int occupancy_f32(int variant, int eos_kind, int bc);
-int occupancy_f64(int variant, int eos_kind, int bc);
-int occupancy_bf16(int variant, int eos_kind, int bc);
-// batched-step units (lb_batch_kernels.cu)
-cudaError_t batch_f32(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
-                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
-                      cudaStream_t st);
-cudaError_t batch_f64(int variant, int eos, bool configure, int *occ, int grid, const void *maps,
-                      const void *lats, const BatchItem *items, int n_items, int phase, int *errs,
-                      cudaStream_t st);
+// tensor_map_in: a CUtensorMap describing the input buffer (3-D: x, y, population plane).
+// Step units, one per storage type and ring kind K (lb_step_<type>.cu: K = 0, whole-row
+// ring; lb_step_<type>_stage.cu: K = 1, stage ring); configure: set the kernel attributes
+// only. A variant of the other kind returns cudaErrorInvalidValue (occupancy 0).
+#define LB_DECLARE_STEP_UNIT(NAME, K)                                                         \
+    cudaError_t step_##NAME##_k##K(const Consts &c, const Geom &g, const StepLaunch &l,      \
+                                   int order, const void *tensor_map_in, void *gout, int *err, \
+                                   cudaStream_t st, bool configure);                         \
+    int occupancy_##NAME##_k##K(int variant, int eos_kind, int bc);
+LB_DECLARE_STEP_UNIT(f32, 0)
+LB_DECLARE_STEP_UNIT(f32, 1)
+LB_DECLARE_STEP_UNIT(f64, 0)
+LB_DECLARE_STEP_UNIT(f64, 1)
+LB_DECLARE_STEP_UNIT(bf16, 0)
+LB_DECLARE_STEP_UNIT(bf16, 1)
+#undef LB_DECLARE_STEP_UNIT
+int step_variant_kind(int variant);   // 0: whole-row ring, 1: stage ring
+// batched-step units (lb_batch_kernels.cu: K = 0, lb_batch_stage.cu: K = 1)
+#define LB_DECLARE_BATCH_UNIT(NAME, K)                                                        \
+    cudaError_t batch_##NAME##_k##K(int variant, int eos, bool configure, int *occ, int grid, \
+                                    const void *maps, const void *lats, const BatchItem *items, \
+                                    int n_items, int phase, int *errs, cudaStream_t st);
+LB_DECLARE_BATCH_UNIT(f32, 0)
+LB_DECLARE_BATCH_UNIT(f32, 1)
+LB_DECLARE_BATCH_UNIT(f64, 0)
+LB_DECLARE_BATCH_UNIT(f64, 1)
+#undef LB_DECLARE_BATCH_UNIT
 
 // order 0 / 1: visit the row blocks (and the rows inside them) forward / in reverse
 cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,

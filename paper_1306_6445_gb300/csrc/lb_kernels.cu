@@ -390,16 +390,23 @@ int step_variant_tx(int variant) {
     return (variant >= 0 && variant < 7) ? tx[variant] : 0;
 }
 
-int step_variant_planes(int variant) { return variant >= 4 ? 3 : 9; }
+int step_variant_kind(int variant) { return variant >= 4 ? 1 : 0; }
+
+int step_variant_planes(int variant) { return step_variant_kind(variant) ? 3 : 9; }
+
+// the launch a new context or batch starts with: the stage ring, 128-column strips, S = 3
+int default_step_variant() { return 4; }
 
 StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, int variant,
                             int rows_override) {
     StepLaunch l;
     l.variant = variant;
     l.tx = step_variant_tx(variant);
-    const int per_sm = prec == LB_FP32   ? occupancy_f32(variant, eos_kind, g.walls)
-                     : prec == LB_BF16 ? occupancy_bf16(variant, eos_kind, g.walls)
-                                       : occupancy_f64(variant, eos_kind, g.walls);
+    const bool st = step_variant_kind(variant) == 1;
+    const int per_sm =
+        prec == LB_FP32 ? (st ? occupancy_f32_k1 : occupancy_f32_k0)(variant, eos_kind, g.walls)
+        : prec == LB_BF16 ? (st ? occupancy_bf16_k1 : occupancy_bf16_k0)(variant, eos_kind, g.walls)
+                          : (st ? occupancy_f64_k1 : occupancy_f64_k0)(variant, eos_kind, g.walls);
     l.ctas_per_sm = std::max(per_sm, 1);
     if (rows_override > 0) {
         l.rows = std::min(rows_override, g.ny);
@@ -417,18 +424,25 @@ StepLaunch make_step_launch(int prec, int eos_kind, const Geom &g, int num_sms, 
     return l;
 }
 
+// the step unit of the storage type and the variant's ring kind
+static cudaError_t launch_step_unit(int prec, const Consts &c, const Geom &g, const StepLaunch &l,
+                                    int order, const void *tmap, void *gout, int *err,
+                                    cudaStream_t st, bool configure) {
+    const bool k1 = step_variant_kind(l.variant) == 1;
+    auto f = prec == LB_FP32 ? (k1 ? step_f32_k1 : step_f32_k0)
+           : prec == LB_BF16 ? (k1 ? step_bf16_k1 : step_bf16_k0)
+                             : (k1 ? step_f64_k1 : step_f64_k0);
+    return f(c, g, l, order, tmap, gout, err, st, configure);
+}
+
 cudaError_t configure_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l) {
     static const CUtensorMap dummy{};
-    if (prec == LB_FP32) return step_f32(c, g, l, 0, &dummy, nullptr, nullptr, nullptr, true);
-    if (prec == LB_BF16) return step_bf16(c, g, l, 0, &dummy, nullptr, nullptr, nullptr, true);
-    return step_f64(c, g, l, 0, &dummy, nullptr, nullptr, nullptr, true);
+    return launch_step_unit(prec, c, g, l, 0, &dummy, nullptr, nullptr, nullptr, true);
 }
 
 cudaError_t launch_step(int prec, const Consts &c, const Geom &g, const StepLaunch &l, int order,
                         const void *tensor_map_in, void *gout, int *err, cudaStream_t st) {
-    if (prec == LB_FP32) return step_f32(c, g, l, order, tensor_map_in, gout, err, st, false);
-    if (prec == LB_BF16) return step_bf16(c, g, l, order, tensor_map_in, gout, err, st, false);
-    return step_f64(c, g, l, order, tensor_map_in, gout, err, st, false);
+    return launch_step_unit(prec, c, g, l, order, tensor_map_in, gout, err, st, false);
 }
 
 cudaError_t launch_unstream(int prec, const Geom &g, const void *f, void *gbuf, bool packed,
@@ -655,22 +669,26 @@ cudaError_t launch_interface_height(int prec, const Consts &c, const Geom &g, co
 
 namespace lbm {
 
+// the batched-step unit of the storage type and the variant's ring kind
+static cudaError_t batch_unit(int prec, int variant, int eos_kind, bool configure, int *occ,
+                              int grid, const void *maps, const void *lats, const BatchItem *items,
+                              int n_items, int phase, int *errs, cudaStream_t st) {
+    const bool k1 = step_variant_kind(variant) == 1;
+    auto f = prec == LB_FP32 ? (k1 ? batch_f32_k1 : batch_f32_k0)
+                             : (k1 ? batch_f64_k1 : batch_f64_k0);
+    return f(variant, eos_kind, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+}
+
 cudaError_t configure_batch(int prec, int eos_kind, int variant, int *ctas_per_sm) {
-    if (prec == LB_FP32)
-        return batch_f32(variant, eos_kind, true, ctas_per_sm, 0, nullptr, nullptr, nullptr, 0, 0,
-                         nullptr, nullptr);
-    return batch_f64(variant, eos_kind, true, ctas_per_sm, 0, nullptr, nullptr, nullptr, 0, 0,
-                     nullptr, nullptr);
+    return batch_unit(prec, variant, eos_kind, true, ctas_per_sm, 0, nullptr, nullptr, nullptr, 0,
+                      0, nullptr, nullptr);
 }
 
 cudaError_t launch_batch_step(int prec, int eos_kind, int variant, int grid, const void *maps,
                               const void *lats, const BatchItem *items, int n_items, int phase,
                               int *errs, cudaStream_t st) {
-    if (prec == LB_FP32)
-        return batch_f32(variant, eos_kind, false, nullptr, grid, maps, lats, items, n_items,
-                         phase, errs, st);
-    return batch_f64(variant, eos_kind, false, nullptr, grid, maps, lats, items, n_items, phase,
-                     errs, st);
+    return batch_unit(prec, variant, eos_kind, false, nullptr, grid, maps, lats, items, n_items,
+                      phase, errs, st);
 }
 
 }  // namespace lbm

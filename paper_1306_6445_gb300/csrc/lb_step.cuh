@@ -765,9 +765,15 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH<T>);
+            if (w == TX) {   // a whole strip (CTA-uniform): every thread stores two sites
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
-                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
+                for (int a = 0; a < 9; ++a)
+                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], true, a, P);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
+            }
             if (BC == 2) {
                 if (x == 0 || x + 1 >= nx - 1) {
                     const unsigned rowi = (unsigned)y * (unsigned)pitch;
@@ -860,7 +866,8 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                                                min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
-    if (bad) atomicOr(err, ERR_DOMAIN);
+    // one flag per CTA (a failing lattice would otherwise send every thread to one word)
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, ERR_DOMAIN);
 }
 
 // Many lattices (periodic) in one launch: a persistent grid walks a fixed list of work
@@ -890,7 +897,7 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
         const int st = march<T, EOS, false, TX, S, G>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
                                                    L.plane, it.x0, it.w, it.yb, it.n,
                                                    phase ? -it.dir : it.dir, smem_raw, bad);
-        if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&errs[it.lat], ERR_DOMAIN);
         if (st) {
             if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
             return;   // the ring is in an unknown state: this CTA stops
@@ -922,7 +929,8 @@ k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ go
                                                   min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                   ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
-    if (bad) atomicOr(err, ERR_DOMAIN);
+    // one flag per CTA (a failing lattice would otherwise send every thread to one word)
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, ERR_DOMAIN);
 }
 
 // Many lattices with the stage ring (as k_batch_step).
@@ -947,7 +955,7 @@ k_batch_step_stage(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *
         const int st = march_stage<T, EOS, 0, TX, S>(map, L.g[phase ^ 1], P, L.nx, L.ny, L.pitch,
                                                      L.plane, it.x0, it.w, it.yb, it.n,
                                                      phase ? -it.dir : it.dir, smem_raw, bad);
-        if (bad) atomicOr(&errs[it.lat], ERR_DOMAIN);
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&errs[it.lat], ERR_DOMAIN);
         if (st) {
             if (threadIdx.x == 0) atomicOr(&errs[it.lat], st);
             return;
@@ -1033,13 +1041,18 @@ cudaError_t step_eos(const Consts &c, const Geom &g, int rows, int order, const 
     X(5, 128, 4, 1)         \
     X(6, 240, 3, 1)
 
-template <typename T>
+// the variants of ring kind K (each kind is compiled in its own translation unit)
+template <typename T, int K>
 cudaError_t step_dispatch(const Consts &c, const Geom &g, const StepLaunch &l, int order,
                           const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                           bool configure) {
     switch (l.variant) {
-#define LB_X(v, tx, s, k) \
-        case v: return step_eos<T, tx, s, k>(c, g, l.rows, order, tin, out, err, st, configure);
+#define LB_X(v, tx, s, k)                                                                   \
+        case v:                                                                             \
+            if constexpr (k == K)                                                           \
+                return step_eos<T, tx, s, k>(c, g, l.rows, order, tin, out, err, st, configure); \
+            else                                                                            \
+                return cudaErrorInvalidValue;
         LB_STEP_VARIANTS(LB_X)
 #undef LB_X
         default: return cudaErrorInvalidValue;
@@ -1078,11 +1091,13 @@ int occupancy_eos(int eos, int bc) {
     }
 }
 
-template <typename T>
+template <typename T, int K>
 int occupancy(int variant, int eos, int w) {
     switch (variant) {
-#define LB_X(v, tx, s, k) \
-        case v: return occupancy_eos<T, tx, s, k>(eos, w);
+#define LB_X(v, tx, s, k)                                        \
+        case v:                                                  \
+            if constexpr (k == K) return occupancy_eos<T, tx, s, k>(eos, w); \
+            else return 0;
         LB_STEP_VARIANTS(LB_X)
 #undef LB_X
         default: return 0;
@@ -1135,19 +1150,49 @@ cudaError_t batch_eos(int eos, bool configure, int *occ, int grid, const void *m
     }
 }
 
-template <typename T>
+template <typename T, int K>
 cudaError_t batch_dispatch(int variant, int eos, bool configure, int *occ, int grid,
                            const void *maps, const void *lats, const BatchItem *items,
                            int n_items, int phase, int *errs, cudaStream_t st) {
     switch (variant) {
-#define LB_X(v, tx, s, k) \
-        case v: return batch_eos<T, tx, s, k>(eos, configure, occ, grid, maps, lats, items, n_items, phase, errs, st);
+#define LB_X(v, tx, s, k)                                                                    \
+        case v:                                                                              \
+            if constexpr (k == K)                                                            \
+                return batch_eos<T, tx, s, k>(eos, configure, occ, grid, maps, lats, items,  \
+                                              n_items, phase, errs, st);                     \
+            else                                                                             \
+                return cudaErrorInvalidValue;
         LB_STEP_VARIANTS(LB_X)
 #undef LB_X
         default: return cudaErrorInvalidValue;
     }
 }
 
+
+
 }  // namespace
 
 }  // namespace lbm
+
+// The entry points of one step unit: the single-lattice step and its occupancy for storage
+// type T and ring kind K (lb_internal.h declares them).
+#define LB_STEP_UNIT(NAME, T, K)                                                                \
+    cudaError_t step_##NAME##_k##K(const Consts &c, const Geom &g, const StepLaunch &l,        \
+                                   int order, const void *tensor_map_in, void *gout, int *err, \
+                                   cudaStream_t st, bool configure) {                          \
+        return step_dispatch<T, K>(c, g, l, order,                                             \
+                                   *static_cast<const CUtensorMap *>(tensor_map_in), gout, err, \
+                                   st, configure);                                             \
+    }                                                                                          \
+    int occupancy_##NAME##_k##K(int variant, int eos_kind, int bc) {                          \
+        return occupancy<T, K>(variant, eos_kind, bc);                                         \
+    }
+
+// The batched step of one unit (storage type T, ring kind K).
+#define LB_BATCH_UNIT(NAME, T, K)                                                              \
+    cudaError_t batch_##NAME##_k##K(int variant, int eos, bool configure, int *occ, int grid,  \
+                                    const void *maps, const void *lats, const BatchItem *items, \
+                                    int n_items, int phase, int *errs, cudaStream_t st) {      \
+        return batch_dispatch<T, K>(variant, eos, configure, occ, grid, maps, lats, items,     \
+                                    n_items, phase, errs, st);                                 \
+    }

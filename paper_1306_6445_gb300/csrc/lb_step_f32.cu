@@ -1,17 +1,9 @@
-// Step kernels with float storage (one translation unit per precision, compiled in parallel).
+// Step kernels with float storage, whole-row ring variants (one translation unit per storage type
+// and ring kind, compiled in parallel).
 #include "lb_step.cuh"
 
 namespace lbm {
 
-cudaError_t step_f32(const Consts &c, const Geom &g, const StepLaunch &l, int order,
-                      const void *tensor_map_in, void *gout, int *err, cudaStream_t st,
-                      bool configure) {
-    return step_dispatch<float>(c, g, l, order, *static_cast<const CUtensorMap *>(tensor_map_in),
-                              gout, err, st, configure);
-}
-
-int occupancy_f32(int variant, int eos_kind, int bc) {
-    return occupancy<float>(variant, eos_kind, bc);
-}
+LB_STEP_UNIT(f32, float, 0)
 
 }  // namespace lbm

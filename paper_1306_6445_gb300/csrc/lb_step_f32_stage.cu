@@ -1,0 +1,9 @@
+// Step kernels with float storage, stage ring variants (one translation unit per storage type
+// and ring kind, compiled in parallel).
+#include "lb_step.cuh"
+
+namespace lbm {
+
+LB_STEP_UNIT(f32, float, 1)
+
+}  // namespace lbm

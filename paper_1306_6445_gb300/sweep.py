@@ -42,10 +42,10 @@ def laplace_points(lbm, points, side: int = 128, radius: float | None = None,
         init.append((rl, rv))
     b = lbm.Batch(descs, prec=prec)
     try:
-        if autotune:
-            b.autotune(2)
         for i, (rl, rv) in enumerate(init):
             b.set_rho_u(i, I.droplet_density(side, side, radius, rl, rv))
+        if autotune:
+            b.autotune(2)   # timed on these states, which it restores
         radii = np.full(n, float(radius))
         b.step(steps - window)
         acc = np.zeros((n, 3))

@@ -70,17 +70,22 @@ def test_batch_equals_single_lattice_runs_bitwise(lbm, prec):
 def test_batch_launch_shapes_and_autotune_agree(lbm):
     descs, rhos, _ = small_batch(lbm)
     outs = []
-    for shape in [(0, 16), (1, 8), (2, 12), (3, 24), None]:
+    for shape in [(0, 16), (1, 8), (2, 12), (3, 24), (4, 12), (5, 8), (6, 16), None]:
         b = lbm.Batch(descs, prec="fp32")
-        if shape is None:
-            v, r = b.autotune(3)
-            assert 0 <= v < lbm.lb_launch_variants() and r > 0
-            assert b.steps_done == 0
-        else:
+        if shape is not None:
             b.set_launch(*shape)
         for i, rr in enumerate(rhos):
             b.set_rho_u(i, rr)
-        b.step(20)
+        b.step(5)
+        if shape is None:
+            # timed on the current states, which it restores with the step count
+            before = [b.populations(i) for i in range(len(descs))]
+            v, r = b.autotune(3)
+            assert 0 <= v < lbm.lb_launch_variants() and r > 0
+            assert b.steps_done == 5
+            for i in range(len(descs)):
+                assert np.array_equal(b.populations(i), before[i])
+        b.step(15)
         outs.append([b.populations(i) for i in range(len(descs))])
         b.close()
     for o in outs[1:]:
