@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--batch-lattices", type=int, default=512)
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-splash", action="store_true", help="skip the splash leg")
-    ap.add_argument("--splash-steps", type=int, default=14000,
-                    help="splash time steps (14000 = t* 1.75, the end of the paper's run)")
+    ap.add_argument("--splash-steps", type=int, default=40000,
+                    help="splash time steps per grid point (40000 = t* 5.05 at D 400, U 0.05)")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate leg (converged sweep, training, checked kappa)")
     return ap.parse_args()
@@ -463,17 +463,15 @@ def surrogate_leg(lbm, torch, n_train=512):
     }
 
 
-def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, We=200.0, Re=500.0, U=0.05,
-               t_over_tc=0.65, steps=None):
-    """Droplet splashing on a thin film at 4096 x 1024 (film 0.1 D, D = 400), FP32, CS at
-    0.65 T_c with sigma_F = 0.087, U = 0.05; Re = U D / nu_L, nu_V = 20 nu_L switched at
-    the mean phase density; the target surface tension follows from We = rho_L U^2 D /
-    sigma, and kappa comes from the surrogate network, checked by one Laplace run
-    (128^2). Reports the kernel rate and the spread radius."""
-    import numpy as np
+def splash_point(lbm, torch, net, nx, ny, D, We, Re, U, t_over_tc, steps):
+    """One droplet-splash run at 4096 x 1024 (film 0.1 D), FP32, CS at t_over_tc T_c with
+    sigma_F = 0.087; Re = U D / nu_L, nu_V = 20 nu_L switched at the mean phase density; the
+    target surface tension follows from We = rho_L U^2 D / sigma, and kappa comes from the
+    surrogate network, checked by one Laplace run (128^2). The run starts at t* = 0.05
+    after the first contact (splash.T0) and goes on for `steps` steps or until the EOS
+    branch is left (recorded). Reports the kernel rate and the spread radius."""
     from paper_1306_6445_gb300 import splash, surrogate
 
-    steps = ARGS.splash_steps if steps is None else steps
     eos = lbm.cs_eos(t_over_tc)
     rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
     sigma_t = rl * U * U * D / We
@@ -486,36 +484,69 @@ def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, We=200.0, Re=500.0, U
                               20.0 * nu_l, 0.5 * (rl + rv), rl, rv)
     lat.autotune(3)
     stream = torch.cuda.current_stream()
-    marks = {int(round(t * D / U)): t for t in (0.25, 0.75, 1.0, 1.5, 1.75)}
+    marks = {splash.steps_to(t, D, U): t for t in (0.25, 0.75, 1.0, 1.5, 1.75, 2.5, 5.0)
+             if splash.steps_to(t, D, U) <= steps}
+    stops = sorted(set(marks) | set(range(1000, steps, 1000)) | {steps})
     radii = {}
     done, failed, ms = 0, None, 0.0
     torch.cuda.synchronize()
     try:
-        for k in range(0, steps, 1000):
-            n = min(1000, steps - k)
+        for stop in stops:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lat.step(n)
+            lat.step(stop - done)
             e1.record(stream)
             lat.sync()                      # an EOS-domain error surfaces here
             ms += e0.elapsed_time(e1)
-            done = k + n
+            done = stop
             if done in marks:
                 radii[marks[done]] = round(splash.spread_radius(lat.rho(), film, D, rl, rv), 4)
     except lbm.LBError as e:
-        failed = f"{lbm.STATUS_NAMES.get(e.status, e.status)} between steps {done} and {done + 1000}"
+        failed = f"{lbm.STATUS_NAMES.get(e.status, e.status)} between steps {done} and {stop}"
     launch = lbm.lb_get_launch(lat.ctx)
     lat.close()
-    return {"workload": f"{nx}x{ny} splash, D={D:.0f}, film {film:.0f}, CS {t_over_tc}Tc, "
-                        f"We={We:.0f}, Re={Re:.0f}, U={U}, FP32, {steps} steps",
-            "kappa_from_surrogate": round(kappa, 5), "sigma_target": sigma_t,
-            "sigma_checked_rel_err": round(float(res["rel_err"][0]), 5),
+    return {"We": We, "Re": Re, "kappa_from_surrogate": round(kappa, 5),
+            "sigma_target": sigma_t, "sigma_checked_rel_err": round(float(res["rel_err"][0]), 5),
             "laplace_runs": int(res["runs"][0]),
             "mlups": round(nx * ny * done / (ms * 1e-3) / 1e6, 1) if done else None,
-            "steps_done": done, "failed": failed, "launch": launch,
-            "t_star_end": round(U * done / D, 3),
+            "steps_done": done, "breakdown": failed, "launch": launch,
+            "t_star_end": round(splash.T0 + U * done / D, 3),
             "spread_radius_over_D_at_t_star": radii,
             "power_law_1p3_sqrt_t": {t: round(1.3 * t ** 0.5, 4) for t in radii}}
+
+
+def splash_leg(lbm, torch, net, nx=4096, ny=1024, D=400.0, U=0.05, t_over_tc=0.65,
+               steps=None):
+    """The droplet-splash workload at 4096 x 1024 over the grid We in {200, 800} x Re in
+    {500, 1000} (D = 400, U = 0.05, CS at 0.65 T_c), each point `steps` steps long."""
+    steps = ARGS.splash_steps if steps is None else steps
+    points = [splash_point(lbm, torch, net, nx, ny, D, We, Re, U, t_over_tc, steps)
+              for We in (200.0, 800.0) for Re in (500.0, 1000.0)]
+    return {"workload": f"{nx}x{ny} splash, D={D:.0f}, film {0.1 * D:.0f}, CS {t_over_tc}Tc, "
+                        f"U={U}, FP32, up to {steps} steps per point, start at t*=0.05",
+            "points": points}
+
+
+def host_cpu():
+    """The host's logical core count and CPU model (lscpu's model name, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
 def cpu_baseline(nx, ny, budget_s=20.0):
@@ -547,9 +578,9 @@ print(json.dumps({"steps": n, "seconds": el, "mlups": nx * ny * n / el / 1e6}))
     if r.returncode != 0:
         return {"value": None, "unit": "MLUPS", "error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": round(d["mlups"], 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{d['steps']} FP64 steps of the full {nx}x{ny} lattice "
-                      f"({d['seconds']:.1f} s, numpy, 1 thread)"}
+    return dict({"value": round(d["mlups"], 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                 "sample": f"{d['steps']} FP64 steps of the full {nx}x{ny} lattice "
+                           f"({d['seconds']:.1f} s, numpy, 1 thread)"}, **host_cpu())
 
 
 def native(args):
@@ -668,15 +699,13 @@ def reference(args):
     from oracle import lattice as OL
     from paper_1306_6445_gb300 import inputs
 
-    # bounded sample of the workload: a 2048 x 128 band of the droplet lattice, periodic,
-    # one LB step per bench step (the oracle needs ~1 s per 3 M site updates)
-    nx, ny = args.nx, min(args.ny, 128)
+    # bounded sample of the workload: the whole droplet lattice (the same lattice as the
+    # native arm and its cpu_baseline), one LB step per bench step (about 1.3 s each at
+    # 2048^2 on one host core)
+    nx, ny = args.nx, args.ny
     eos = OE.cs_eos(0.8)
     rv, rl, _ = OE.maxwell(eos, -1.0)
-    rho_full = inputs.droplet_density(args.nx, args.ny, 200.0 * min(args.nx, args.ny) / 2048.0,
-                                      rl, rv)
-    y0 = args.ny // 2 - ny // 2
-    rho = rho_full[y0:y0 + ny]
+    rho = inputs.droplet_density(nx, ny, 200.0 * min(nx, ny) / 2048.0, rl, rv)
     f = OL.equilibrium(rho, 0 * rho, 0 * rho)
     p = OL.Params(eos=eos, G=-1.0, kappa=0.6, rates=OL.Rates.from_viscosity(0.1))
     for _ in range(args.warmup):
@@ -686,7 +715,7 @@ def reference(args):
         f = OL.step(f, p)
     el = time.perf_counter() - t
     v = nx * ny * args.steps / el / 1e6
-    sample = f"{args.steps} FP64 steps of a {nx}x{ny} band of the droplet lattice (numpy, 1 thread)"
+    sample = f"{args.steps} FP64 steps of the full {nx}x{ny} droplet lattice (numpy, 1 thread)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
@@ -695,9 +724,9 @@ def reference(args):
         "data": "synthetic",
         "config": dict(bench_config(args.nx, args.ny, args.inner,
                                     int(os.environ.get("WORLD_SIZE", "1"))),
-                       sample=f"{nx}x{ny} band, 1 LB step per bench step"),
-        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                       sample=f"the full {nx}x{ny} lattice, 1 LB step per bench step"),
+        "cpu_baseline": dict({"value": round(v, 4), "unit": "MLUPS", "cores": 1,
+                              "kind": "oracle", "sample": sample}, **host_cpu()),
         "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)

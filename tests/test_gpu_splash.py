@@ -3,9 +3,9 @@ droplet R = 50 moving down at U = 0.125, Eq. 23 fluid (density ratio 100, sigma_
 Re = U D / nu_L = 1000, nu_V / nu_L = 20 switched at rho_1 = 1.49, MRT rates of Sec. V.C,
 a no-slip bottom wall and open boundaries elsewhere (LB_BC_OPEN).
 
-The paper does not define its spread radius; it is read here as the largest distance from
-the impact axis of liquid (rho above the mean of the phase densities) in the row 0.1 D
-above the undisturbed film surface. The droplet starts 2 lattice units above the film."""
+Readings of `splash` (the paper states neither): the run starts at t* = 0.05 after the first
+contact, with the droplet already 0.05 D inside the film; the spread radius is the outer
+edge of the film-connected liquid in the row 0.1 D above the undisturbed film."""
 import json
 import os
 
@@ -36,38 +36,43 @@ def lbm():
     return mod
 
 
-def spread_radii(lbm, kappa, tstars, prec="fp32"):
+def spread_radii(lbm, kappa, tstars, prec="fp32", t_end=None):
     from paper_1306_6445_gb300 import splash
     nu_l = U * D / 1000.0
     lat = splash.make_lattice(lbm, NX, NY, lbm.EOSParams(kind="piecewise"), -1.0, kappa, 0.087,
                               D, FILM, U, nu_l, 20.0 * nu_l, 1.49, 100.0, 1.0, prec=prec)
     out, done = [], 0
     for ts in tstars:
-        n = int(round(ts * D / U))
+        n = splash.steps_to(ts, D, U)
         lat.step(n - done)
         done = n
         out.append(splash.spread_radius(lat.rho(), FILM, D, 100.0, 1.0))
+    if t_end is not None:               # run on; an EOS-domain error would raise here
+        lat.step(splash.steps_to(t_end, D, U) - done)
+        lat.sync()
     lat.close()
     return np.array(out)
 
 
-def test_spread_radius_follows_table5_and_the_power_law(lbm):
+def test_spread_radius_follows_table5_for_both_surface_tensions(lbm):
+    """1 - kappa = 1 (We = 97) and 1 - kappa = 0.05 (We = 1953, Sec. V.C): both run to
+    t* = 1.75 (the end of Fig. 5 and Fig. 6), follow their Table 5 column within 5 %, and
+    differ from each other by under 2 % (the paper's conclusion: the surface tension barely
+    changes the spread radius)."""
     ts = np.array(T5["t_star"][1:])                 # 0.25, 0.75, 1.0, 1.5
-    r0 = spread_radii(lbm, 0.0, ts)
-    r1 = spread_radii(lbm, 0.75, ts)
-    print("t*", ts, "r/D (1-kappa = 1)", r0, "(1-kappa = 0.25)", r1,
-          "Table 5", T5["r_over_D_one_minus_kappa_1"][1:])
+    r1 = spread_radii(lbm, 0.0, ts, t_end=1.75)
+    r005 = spread_radii(lbm, 0.95, ts, t_end=1.75)
+    print("t*", ts, "r/D (1-kappa = 1)", r1, "(1-kappa = 0.05)", r005,
+          "Table 5", T5["r_over_D_one_minus_kappa_1"][1:], T5["r_over_D_one_minus_kappa_0p05"][1:])
+    assert np.all(np.abs(r1 / np.array(T5["r_over_D_one_minus_kappa_1"][1:]) - 1) < 0.05)
+    assert np.all(np.abs(r005 / np.array(T5["r_over_D_one_minus_kappa_0p05"][1:]) - 1) < 0.05)
+    assert np.all(np.abs(r005 / r1 - 1) < 0.02)
     # the power law r/D ~ 1.3 sqrt(t*) (the paper's own values lie within 4 % of it)
-    assert np.all(np.abs(r0 / (1.3 * np.sqrt(ts)) - 1) < 0.06)
-    # Table 5, 1 - kappa = 1, within 5 % (open-boundary type, start gap and the radius
-    # measure are readings)
-    assert np.all(np.abs(r0 / np.array(T5["r_over_D_one_minus_kappa_1"][1:]) - 1) < 0.05)
-    # the surface tension barely changes the spread radius (Table 5's conclusion)
-    assert np.all(np.abs(r1 / r0 - 1) < 0.03)
+    assert np.all(np.abs(r1 / (1.3 * np.sqrt(ts)) - 1) < 0.06)
 
 
 def test_fp32_and_fp64_spread_radii_agree(lbm):
     ts = np.array([0.25, 1.0])
-    a = spread_radii(lbm, 0.0, ts, "fp32")
-    b = spread_radii(lbm, 0.0, ts, "fp64")
-    assert np.all(np.abs(a - b) <= 2.0 / D)         # within two lattice units
+    a = spread_radii(lbm, 0.95, ts, "fp32")
+    b = spread_radii(lbm, 0.95, ts, "fp64")
+    assert np.all(np.abs(a - b) <= 1.0 / D)         # within one lattice unit

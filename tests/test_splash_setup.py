@@ -31,17 +31,46 @@ def test_splash_state_geometry():
     assert rho[y_gap, nx // 2] < rho[yc, nx // 2]
 
 
-def test_spread_radius_reads_the_row_above_the_film():
+def test_splash_state_overlapping_start():
+    # a negative gap starts the droplet inside the film (the start of a splash run): the
+    # droplet and the film are one liquid body on the axis, with no vapour between them
+    nx, ny, film, R, U, rl, rv = 600, 225, 25.0, 50.0, 0.125, 100.0, 1.0
+    rho, _, uy = I.splash_state(nx, ny, film, R, -5.0, U, rl, rv)
+    axis = rho[:, nx // 2]
+    assert np.all(axis[: int(film + 2 * R - 5) - 2] > 0.5 * (rl + rv))
+    assert uy[int(film + R - 5), nx // 2] == pytest.approx(-U, rel=1e-6)
+
+
+def test_steps_to_counts_from_the_start_time():
+    # t* = t0 + U t / D with t0 = 0.05: t* = 0.25 is 160 steps after the start at D = 100
+    assert splash.T0 == 0.05
+    assert splash.steps_to(0.25, 100.0, 0.125) == 160
+    assert splash.steps_to(splash.T0, 100.0, 0.125) == 0
+
+
+def test_spread_radius_reads_the_film_connected_liquid_above_the_film():
     nx, ny, film, D, rl, rv = 200, 80, 10.0, 40.0, 100.0, 1.0
+    mid = 0.5 * (rl + rv)
     rho = np.full((ny, nx), rv)
-    row = int(film + 0.1 * D)          # row 14
-    rho[row, 100 - 30:100 + 21] = rl   # liquid from x = 70 to 120: farthest |x - 100| = 30
-    assert splash.spread_radius(rho, film, D, rl, rv) == pytest.approx(30 / D)
-    # liquid elsewhere (other rows) does not count
-    rho2 = np.full((ny, nx), rv)
-    rho2[row + 1, 0:nx] = rl
-    rho2[row - 1, 0:nx] = rl
-    assert splash.spread_radius(rho2, film, D, rl, rv) == 0.0
-    # a detached drop on the row farther out counts (secondary droplets do)
+    rho[: int(film)] = rl                       # the film, rows 0..9
+    row = int(film + 0.1 * D)                   # row 14
+    rho[int(film):row + 1, 85:121] = rl         # a liquid column standing on the film
+    # liquid from x = 85 to 120 with vapour beyond: rho crosses mid halfway to the next
+    # site, at 84.5 and 120.5, so the farther edge is 20.5 from the axis x = 100
+    assert splash.spread_radius(rho, film, D, rl, rv) == pytest.approx(20.5 / D)
+    # a partly filled site beyond the edge moves the edge by the linear crossing of mid
+    rho[row, 121] = rv + 0.5 * (mid - rv)       # a quarter of the way from rv to rl
+    # crossing between x = 120 (rl) and 121: 120 + (rl - mid) / (rl - rho[121])
+    edge = 120 + (rl - mid) / (rl - rho[row, 121])
+    assert splash.spread_radius(rho, film, D, rl, rv) == pytest.approx((edge - 100) / D)
+    # a detached drop on the row, farther out, does not count (no liquid path to the film)
     rho[row, 185] = rl
-    assert splash.spread_radius(rho, film, D, rl, rv) == pytest.approx(85 / D)
+    assert splash.spread_radius(rho, film, D, rl, rv) == pytest.approx((edge - 100) / D)
+    # liquid connected to the film only through a diagonal does not count (4-neighbours)
+    rho2 = np.full((ny, nx), rv)
+    rho2[: int(film)] = rl
+    rho2[row, 150] = rl
+    rho2[row - 1, 151] = rl
+    for y in range(int(film), row - 1):
+        rho2[y, 151] = rl
+    assert splash.spread_radius(rho2, film, D, rl, rv) == pytest.approx(0.0)
