@@ -62,7 +62,7 @@ def test_table2_exponential_potential_droplets(lbm):
     t2 = GOLD["table2_exp_psi"]
     fig2 = GOLD["fig2_densities_exp_psi"]
     res = {k: droplet(lbm, eos, -40.0, 120, 40.0, ml, mv, k, 0.0, 0.1, "fp64", 45000)
-           for k in (0.0, 0.5, 0.95)}
+           for k in (0.0, 0.5, 0.95, 0.99)}
     d0 = res[0.0]
     # coexistence densities at kappa = 0: 517.5 / 80.1, ratio 6.461
     assert d0["rho_in"] == pytest.approx(fig2["rho_l"][0], rel=3e-3)
@@ -74,8 +74,15 @@ def test_table2_exponential_potential_droplets(lbm):
     # theta follows (1 - kappa) (Eq. 22) to within 5 % up to kappa = 0.95
     for k in (0.5, 0.95):
         assert res[k]["theta"] / d0["theta"] == pytest.approx(1 - k, rel=0.05)
+    # kappa = 0.95 and 0.99: the surface tension left is a higher-order term. The paper's
+    # own values there fall below (1 - kappa) theta(0) by 0.8 % and 0.6 % of theta(0); the
+    # printed values are matched to 1.2 % of theta(0) (an absolute tolerance of that size),
+    # and theta keeps falling towards zero
+    for k, t_paper in zip(t2["kappa"][2:], t2["surface_tension"][2:]):
+        assert abs(res[k]["theta"] - t_paper) < 0.012 * t2["surface_tension"][0]
+    assert 0 < res[0.99]["theta"] < res[0.95]["theta"] < res[0.5]["theta"]
     # the density ratio moves by less than 1 % (paper: 0.8 % over kappa in [0, 0.99])
-    for k in (0.5, 0.95):
+    for k in (0.5, 0.95, 0.99):
         r = res[k]["rho_in"] / res[k]["rho_out"]
         assert r == pytest.approx(d0["rho_in"] / d0["rho_out"], rel=0.01)
     for d in res.values():
@@ -86,12 +93,17 @@ def test_table3_piecewise_eos_droplets(lbm):
     """Sec. V.A, Table 3: EOS of Eq. 23, G = -1, sigma = 0.087 (Eq. 8), R = 40."""
     eos = lbm.EOSParams(kind="piecewise")
     t3 = GOLD["table3_colosqui"]
-    for i, omk in enumerate(t3["one_minus_kappa"][:3]):
+    for i, omk in enumerate(t3["one_minus_kappa"]):
         d = droplet(lbm, eos, -1.0, 128, 40.0, 100.0, 1.0, 1 - omk, 0.087, 0.1, "fp64", 30000)
         assert d["rho_in"] == pytest.approx(t3["rho_l"][i], rel=1e-3)
         assert d["rho_out"] == pytest.approx(t3["rho_v"][i], rel=0.01)
-        tol = 0.01 if omk >= 0.5 else 0.05
-        assert d["theta"] == pytest.approx(t3["surface_tension"][i], rel=tol)
+        if omk >= 0.05:
+            tol = 0.01 if omk >= 0.5 else 0.05
+            assert d["theta"] == pytest.approx(t3["surface_tension"][i], rel=tol)
+        else:
+            # 1 - kappa = 0.01: the higher-order residual (see the Table 2 test); within
+            # 1.2 % of theta at kappa = 0
+            assert abs(d["theta"] - t3["surface_tension"][i]) < 0.012 * t3["surface_tension"][0]
         assert d["mass_drift"] < 1e-12
 
 
@@ -137,13 +149,17 @@ def capillary_period(lbm, one_minus_kappa, steps=18000, every=50):
 def test_capillary_wave_periods_follow_dispersion_relation(lbm):
     """Sec. V.B, Table 4: L = 160, H = 3.5 L, h0 = 0.125 L, nu = 0.01, rho_L/rho_V = 100,
     walls in y. The periods agree with the analytical periods (Eq. 24 read with omega^2)
-    to within 2 % (the paper's own errors: 3.3 %, 0.9 %)."""
+    to within 2.5 % (the paper's own errors: 3.3 %, 0.9 %, 3.5 %), and at 1 - kappa = 0.25
+    within 2 % of the paper's numerical period. Runs cover about two periods."""
     t4 = GOLD["table4_capillary"]
-    for i, omk in enumerate(t4["one_minus_kappa"][:2]):
-        T, h0 = capillary_period(lbm, omk)
-        print(f"capillary 1-kappa={omk}: period {T:.1f} (analytical {t4['analytical_period'][i]})")
+    for i, omk in enumerate(t4["one_minus_kappa"]):
+        T, h0 = capillary_period(lbm, omk, steps=int(2.3 * t4["analytical_period"][i]))
+        print(f"capillary 1-kappa={omk}: period {T:.1f} (analytical {t4['analytical_period'][i]},"
+              f" paper {t4['numerical_period'][i]})")
         assert h0 == pytest.approx(0.125 * t4["wavelength"], abs=1.0)
-        assert T == pytest.approx(t4["analytical_period"][i], rel=0.02)
+        assert T == pytest.approx(t4["analytical_period"][i], rel=0.025)
+        if omk == 0.25:
+            assert T == pytest.approx(t4["numerical_period"][i], rel=0.02)
 
 
 def test_fp32_matches_fp64_on_a_converged_droplet(lbm):
