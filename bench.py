@@ -283,25 +283,9 @@ def time_e2e(lbm, torch, inputs, nx, ny, inner, steps, warmup):
     return el, bi, bo
 
 
-def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=6, dist=None):
-    """The batched Laplace-law sweep: n_lat periodic droplet lattices drawn with the given
-    seed (side U{64..512 step 32}, R/side U[0.15, 0.35], T/Tc U[0.65, 0.95], kappa
-    U[0, 0.95], tau_v U[0.6, 1.2]; CS a=1 b=4 R=1, G=-1, sigma_F=0.087, Maxwell initial
-    densities, FP32), `steps` time steps each, in one persistent launch per step replayed
-    from CUDA graphs. Compared with running `sample` of the lattices one by one through
-    lb_step (extrapolated to all), and with FP64 single-lattice runs of `check` small ones
-    (surface tension error, both measured on the GPU by lb_batch_measure).
-
-    Under torchrun the lattices are split across ranks (independent problems, no
-    data-path communication, site counts balanced); every rank times its own batch and
-    the whole-job rate uses the slowest rank's time (weak scaling in lattices)."""
-    import numpy as np
-    from paper_1306_6445_gb300 import shard
-    world = dist.get_world_size() if dist is not None else 1
-    rank = dist.get_rank() if dist is not None else 0
-    all_draws = inputs.batch_draws(n_lat, seed)
-    mine = shard.assign([d["side"] ** 2 for d in all_draws], world)[rank]
-    draws = [all_draws[i] for i in mine]
+def batch_setup(lbm, inputs, draws):
+    """Lattice descriptors and initial densities of sweep draws: CS a=1 b=4 R=1, G=-1,
+    sigma_F=0.087, Maxwell initial densities."""
     descs, rhos = [], []
     for d in draws:
         eos = lbm.cs_eos(d["t_over_tc"])
@@ -309,11 +293,51 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
         descs.append(lbm.LatticeDesc(d["side"], d["side"], eos, -1.0, kappa=d["kappa"],
                                      sigma_force=0.087,
                                      rates=lbm.RateParams(s_v=1.0 / d["tau_v"])))
-        rhos.append((d["radius"], rl, rv))
-    radii = np.array([r[0] for r in rhos])
+        rhos.append(inputs.droplet_density(d["side"], d["side"], d["radius"], rl, rv))
+    return descs, rhos
+
+
+def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, dist=None):
+    """The batched Laplace-law sweep: n_lat periodic droplet lattices drawn with the given
+    seed (side U{64..512 step 32}, R/side U[0.15, 0.35], T/Tc U[0.65, 0.95], kappa
+    U[0, 0.95], tau_v U[0.6, 1.2]; CS a=1 b=4 R=1, G=-1, sigma_F=0.087, Maxwell initial
+    densities, FP32) in one persistent launch per step replayed from CUDA graphs.
+
+    throughput_10k: `steps` steps of every lattice, against `sample` of the lattices run one
+    by one through lb_step (extrapolated to all).
+    converged: every lattice runs for its own step budget (0.5 side^2, at least 8192;
+    sweep.step_budget) and is retired when done, its surface tension averaged over its last
+    2048 steps and checked against the same average at 3/4 of the budget (converged when
+    they agree within 1 %); compared with one lattice per side run alone through lb_step
+    under the same protocol (extrapolated by side), and with FP64 batched runs of one lattice
+    each of sides 64, 128, 256, 384 and 512 (surface-tension error of the FP32 batch).
+
+    Under torchrun the lattices are split across ranks (independent problems, no
+    data-path communication, site counts balanced); every rank times its own batch and
+    the whole-job rates use the slowest rank's time (weak scaling in lattices)."""
+    import numpy as np
+    from paper_1306_6445_gb300 import shard, sweep
+    world = dist.get_world_size() if dist is not None else 1
+    rank = dist.get_rank() if dist is not None else 0
+    all_draws = inputs.batch_draws(n_lat, seed)
+    mine = shard.assign([d["side"] ** 2 for d in all_draws], world)[rank]
+    draws = [all_draws[i] for i in mine]
+    descs, rhos = batch_setup(lbm, inputs, draws)
+    radii = np.array([d["radius"] for d in draws])
+    sides = np.array([d["side"] for d in draws])
+    sites_all = sum(d["side"] ** 2 for d in all_draws)
+
+    def slowest(el):
+        if dist is not None:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        return el
+
+    # ---- fixed step count (throughput)
     b = lbm.Batch(descs, prec="fp32")
-    for i, (d, (R, rl, rv)) in enumerate(zip(descs, rhos)):
-        b.set_rho_u(i, inputs.droplet_density(d.nx, d.ny, R, rl, rv))
+    for i, r in enumerate(rhos):
+        b.set_rho_u(i, r)
     # the library's batch autotuner, timed on these states (it restores them)
     variant, rows = b.autotune(3)
     torch.cuda.synchronize()
@@ -322,18 +346,11 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
     t0 = time.perf_counter()
     b.step(steps)
     b.sync()
-    el = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([el], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el = float(tt.item())
+    el = slowest(time.perf_counter() - t0)
     meas = b.measure(radii)
-    table = shard.gather_rows(meas, mine, n_lat, dist)   # every lattice's measurement
+    failed = int(shard.gather_rows(meas, mine, n_lat, dist)[:, 7].sum())
     launch = b.launch()
     b.close()
-    failed = int(table[:, 7].sum())
-    sites_all = sum(d["side"] ** 2 for d in all_draws)
-    # this rank's lattices one by one (a random sample, extrapolated)
     rng = np.random.default_rng(seed + 1)
     pick = rng.choice(len(descs), size=min(sample, len(descs)), replace=False)
     t_seq = 0.0
@@ -341,8 +358,7 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
         d = descs[i]
         lat = lbm.Lattice(d.nx, d.ny, d.eos, d.G, kappa=d.kappa, sigma_force=d.sigma_force,
                           rates=d.rates, prec="fp32")
-        R, rl, rv = rhos[i]
-        lat.set_rho_u(inputs.droplet_density(d.nx, d.ny, R, rl, rv))
+        lat.set_rho_u(rhos[i])
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         lat.step(steps)
@@ -350,29 +366,82 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, check=
         t_seq += time.perf_counter() - t1
         lat.close()
     seq_per_lattice = t_seq / len(pick)
-    # surface tension of the FP32 batch against FP64 single-lattice runs (small lattices)
-    small = [i for i in np.argsort([d.nx for d in descs]) if meas[i, 7] == 0][:check]
-    errs = []
-    for i in small:
-        d = descs[i]
-        R, rl, rv = rhos[i]
-        one = lbm.Batch([d], prec="fp64")
-        one.set_rho_u(0, inputs.droplet_density(d.nx, d.ny, R, rl, rv))
-        one.step(steps)
-        th64 = one.measure(np.array([R]))[0, 0]
-        one.close()
-        errs.append(abs(meas[i, 0] - th64) / abs(th64))
-    return {
-        "lattices": n_lat, "steps": steps, "sites": sites_all, "failed": failed,
-        "ranks": world, "seconds": round(el, 4),
+    throughput = {
+        "steps": steps, "seconds": round(el, 4), "failed": failed,
         "droplets_per_s": round(n_lat / el, 2),
         "mlups": round(sites_all * steps / el / 1e6, 1),
         "sequential_droplets_per_s": round(world / seq_per_lattice, 2),
         "speedup_vs_sequential": round(seq_per_lattice * n_lat / (el * world), 2),
-        "sigma_rel_err_vs_fp64_max": round(float(max(errs)), 6) if errs else None,
-        "sigma_err_sample": len(errs),
-        "launch": launch, "autotuned": {"variant": variant, "rows": rows},
-        "theta_median": float(np.median(table[table[:, 7] == 0, 0])) if failed < n_lat else None,
+        "launch": launch, "autotuned": {"variant": variant, "rows": rows}}
+
+    # ---- every lattice to its own converged budget
+    budgets = np.array([sweep.step_budget(int(s)) for s in sides])
+    b = lbm.Batch(descs, prec="fp32")
+    for i, r in enumerate(rhos):
+        b.set_rho_u(i, r)
+    b.autotune(3)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    res = sweep.converged_readings(b, budgets, radii)
+    torch.cuda.synchronize()
+    el_c = slowest(time.perf_counter() - t0)
+    b.close()
+    rows_c = np.stack([res["theta"], res["converged"], res["failed"]], axis=1)
+    table = shard.gather_rows(rows_c, mine, n_lat, dist)
+    n_conv = int(table[:, 1].sum())
+    lu_all = float(sum(d["side"] ** 2 * sweep.step_budget(d["side"]) for d in all_draws))
+    # one lattice per side alone through lb_step under the same protocol
+    t_side = {}
+    for s_ in sorted(set(sides.tolist())):
+        i = int(np.flatnonzero(sides == s_)[0])
+        d = descs[i]
+        lat = lbm.Lattice(d.nx, d.ny, d.eos, d.G, kappa=d.kappa, sigma_force=d.sigma_force,
+                          rates=d.rates, prec="fp32")
+        lat.set_rho_u(rhos[i])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sweep.converged_single(lat, int(budgets[i]), float(radii[i]))
+        t_side[s_] = time.perf_counter() - t1
+        lat.close()
+    t_seq_c = float(sum(t_side[int(s_)] for s_ in sides))
+    # FP64 batched reference of one lattice each of five sides spanning the range
+    err = None
+    if rank == 0:
+        ref_idx = []
+        for s_ in (64, 128, 256, 384, 512):
+            hits = [k for k, d in enumerate(all_draws) if d["side"] == s_]
+            if hits:
+                ref_idx.append(hits[0])
+        rdraws = [all_draws[k] for k in ref_idx]
+        rdescs, rrhos = batch_setup(lbm, inputs, rdraws)
+        b64 = lbm.Batch(rdescs, prec="fp64")
+        for i, r in enumerate(rrhos):
+            b64.set_rho_u(i, r)
+        r64 = sweep.converged_readings(b64, [sweep.step_budget(d["side"]) for d in rdraws],
+                                       [d["radius"] for d in rdraws])
+        b64.close()
+        e = np.abs(table[ref_idx, 0] / r64["theta"] - 1.0)
+        err = {"sides": [d["side"] for d in rdraws],
+               "rel_err": [round(float(x), 6) for x in e],
+               "max": round(float(e.max()), 6), "within_1pct": int((e <= 0.01).sum())}
+    return {
+        "lattices": n_lat, "sites": sites_all, "ranks": world,
+        "throughput_10k": throughput,
+        "converged": {
+            "protocol": "per-lattice budget 0.5 side^2 steps (>= 8192), retired when done; "
+                        "sigma = mean of the last 2048 steps, converged if within 1 % of the "
+                        "same mean at 3/4 of the budget",
+            "seconds": round(el_c, 3), "lattice_updates": lu_all,
+            "mlups": round(lu_all / el_c / 1e6, 1),
+            "converged": n_conv, "converged_fraction": round(n_conv / n_lat, 4),
+            "failed": int(table[:, 2].sum()),
+            "droplets_per_s_converged": round(n_conv / el_c, 2),
+            "sequential_seconds_estimate": round(t_seq_c, 3),
+            "speedup_vs_sequential": round(t_seq_c / el_c, 2),
+            "sigma_rel_err_vs_fp64": err,
+            "theta_median": float(np.median(table[table[:, 1] == 1, 0])) if n_conv else None},
     }
 
 

@@ -337,6 +337,19 @@ lb_status lb_batch_set_launch(lb_batch *b, int variant, int rows);
 lb_status lb_batch_get_launch(const lb_batch *b, int *variant, int *rows, int *grid,
                               int *items);
 
+/* Choose which lattices lb_batch_step advances (active[i] != 0), for example to stop the
+ * lattices that have converged while the others run on; an inactive lattice keeps its
+ * state, can still be read and measured, and can be made active again. All lattices start
+ * active. Must be called when the batch's step count is even (every multiple of 64 steps
+ * is); rebuilds the work list and drops the captured graphs. Synchronises.
+ * Errors: LB_EINVAL (NULL or an odd step count), LB_ENOMEM, LB_ECUDA. Library plumbing
+ * (the paper has no counterpart). */
+lb_status lb_batch_set_active(lb_batch *b, const unsigned char *active);
+
+/* Steps lattice i has been advanced (it is not advanced while inactive); -1 for a bad i. */
+long long lb_batch_lattice_steps(const lb_batch *b, int i);
+
+/* Steps of the batch as a whole (every lb_batch_step call counts, active lattices or not). */
 long long lb_batch_steps_done(const lb_batch *b);
 int lb_batch_size(const lb_batch *b);
 const char *lb_batch_last_error(const lb_batch *b);

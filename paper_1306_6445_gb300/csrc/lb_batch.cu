@@ -40,7 +40,9 @@ struct BatchCommon {
     double *d_radius = nullptr;
     double *d_meas = nullptr;
     int variant = 0, rows = 16, grid = 0, ctas_per_sm = 1, num_sms = 0;
-    int phase = 0;                       // which buffer holds the current state
+    int phase = 0;                       // which buffer holds the active lattices' state
+    std::vector<unsigned char> active;   // lattices stepped by lb_batch_step
+    std::vector<long long> lat_steps;    // steps taken by each lattice
     long long steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // kGraphSteps steps from phase 0 / 1
     lb_status sticky = LB_OK;
@@ -99,6 +101,7 @@ bool make_items(const lb_batch *b, int tx, int rows, std::vector<lbm::BatchItem>
     items.clear();
     std::vector<int> widths(4096);
     for (int i = 0; i < b->n; ++i) {
+        if (!b->active[i]) continue;     // an inactive lattice has no work items
         const int nx = b->geom[i].nx, ny = b->geom[i].ny;
         const int ns = lb_strip_widths(nx, tx, widths.data(), (int)widths.size());
         if (ns <= 0) return false;
@@ -175,6 +178,10 @@ lb_status apply_batch_launch(lb_batch *b, int variant, int rows) {
     return LB_OK;
 }
 
+// the buffer holding lattice i's state: an inactive lattice was set inactive at an even
+// step count, so its state stays in buffer 0
+int cur(const lb_batch *b, int i) { return b->active[i] ? b->phase : 0; }
+
 template <typename T>
 lb_status upload_lattices(lb_batch *b) {
     std::vector<lbm::BatchLattice<T>> t(b->n);
@@ -186,19 +193,27 @@ lb_status upload_lattices(lb_batch *b) {
         t[i].ny = b->geom[i].ny;
         t[i].pitch = b->geom[i].pitch;
         t[i].plane = (unsigned)b->geom[i].plane;
+        t[i].frozen = b->active[i] ? 0 : 1;
     }
-    LB_BCUDA(b, cudaMalloc(&b->d_lats, t.size() * sizeof(t[0])));
+    if (!b->d_lats) LB_BCUDA(b, cudaMalloc(&b->d_lats, t.size() * sizeof(t[0])));
     LB_BCUDA(b, cudaMemcpy(b->d_lats, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice));
     return LB_OK;
 }
 
+void count_steps(lb_batch *b, int n) {
+    b->steps += n;
+    for (int i = 0; i < b->n; ++i)
+        if (b->active[i]) b->lat_steps[i] += n;
+}
+
 lb_status launch_steps(lb_batch *b, int n) {
     for (int i = 0; i < n; ++i) {
-        LB_BCUDA(b, lbm::launch_batch_step(b->prec, b->eos_kind, b->variant, b->grid, b->d_maps,
-                                           b->d_lats, b->d_items, b->n_items, b->phase,
-                                           b->d_errs, b->stream));
+        if (b->n_items > 0)
+            LB_BCUDA(b, lbm::launch_batch_step(b->prec, b->eos_kind, b->variant, b->grid,
+                                               b->d_maps, b->d_lats, b->d_items, b->n_items,
+                                               b->phase, b->d_errs, b->stream));
         b->phase ^= 1;
-        ++b->steps;
+        count_steps(b, 1);
     }
     return LB_OK;
 }
@@ -348,6 +363,8 @@ lb_status lb_batch_create(lb_batch **out, int n, const lb_lattice_desc *descs, i
         lb_batch_free(b);
         return LB_ENOMEM;
     }
+    b->active.assign(n, 1);
+    b->lat_steps.assign(n, 0);
     s = prec == LB_FP32 ? upload_lattices<float>(b) : upload_lattices<double>(b);
     if (s == LB_OK) s = apply_batch_launch(b, lbm::default_step_variant(), 16);
     if (s != LB_OK) {
@@ -397,6 +414,7 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *row
     }
     const int phase0 = b->phase;
     const long long steps0 = b->steps;
+    const std::vector<long long> lat_steps0 = b->lat_steps;
     const int v0 = b->variant, r0 = b->rows;
     cudaError_t e = cudaMemcpyAsync(saved, b->pool, total, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess)
@@ -437,6 +455,7 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, int *variant, int *row
     cudaFree(saved_errs);
     b->phase = phase0;
     b->steps = steps0;
+    b->lat_steps = lat_steps0;
     if (e != cudaSuccess) return bfail(b, LB_ECUDA, cudaGetErrorString(e));
     if (e2 != cudaSuccess) return bfail(b, LB_ECUDA, cudaGetErrorString(e2));
     lb_status s = apply_batch_launch(b, bv, br);
@@ -457,10 +476,10 @@ lb_status lb_batch_set_rho_u(lb_batch *b, int i, const double *rho, const double
     LB_BCUDA(b, cudaMemcpyAsync(b->d_stage + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     // the per-lattice error word doubles as the init kernel's domain flag
     LB_BCUDA(b, lbm::launch_init_feq(b->prec, b->consts[i], g, b->d_stage, b->d_stage + n,
-                                     b->d_stage + 2 * n, buf(b, i, b->phase ^ 1), b->d_errs + i,
+                                     b->d_stage + 2 * n, buf(b, i, cur(b, i) ^ 1), b->d_errs + i,
                                      b->stream));
-    LB_BCUDA(b, lbm::launch_unstream(b->prec, g, buf(b, i, b->phase ^ 1), buf(b, i, b->phase), false,
-                                     b->stream));
+    LB_BCUDA(b, lbm::launch_unstream(b->prec, g, buf(b, i, cur(b, i) ^ 1), buf(b, i, cur(b, i)),
+                                     false, b->stream));
     LB_BCUDA(b, cudaStreamSynchronize(b->stream));
     int e = 0;
     LB_BCUDA(b, cudaMemcpy(&e, b->d_errs + i, sizeof(int), cudaMemcpyDeviceToHost));
@@ -473,10 +492,12 @@ lb_status lb_batch_step(lb_batch *b, int n) {
     if (!b || n < 0) return LB_EINVAL;
     if (b->sticky != LB_OK) return b->sticky;
     while (n >= kGraphSteps) {
-        lb_status s = ensure_graph(b, b->phase);
-        if (s != LB_OK) return s;
-        LB_BCUDA(b, cudaGraphLaunch(b->graph[b->phase], b->stream));
-        b->steps += kGraphSteps;   // even: the phase is unchanged
+        if (b->n_items > 0) {
+            lb_status s = ensure_graph(b, b->phase);
+            if (s != LB_OK) return s;
+            LB_BCUDA(b, cudaGraphLaunch(b->graph[b->phase], b->stream));
+        }
+        count_steps(b, kGraphSteps);   // even: the phase is unchanged
         n -= kGraphSteps;
     }
     return launch_steps(b, n);
@@ -501,7 +522,7 @@ lb_status lb_batch_get_rho(lb_batch *b, int i, double *rho) {
     if (b->sticky != LB_OK) return b->sticky;
     const lbm::Geom &g = b->geom[i];
     const size_t n = (size_t)g.nx * g.ny;
-    LB_BCUDA(b, lbm::launch_macro_fields(b->prec, b->consts[i], g, buf(b, i, b->phase), nullptr,
+    LB_BCUDA(b, lbm::launch_macro_fields(b->prec, b->consts[i], g, buf(b, i, cur(b, i)), nullptr,
                                          b->d_stage, nullptr, nullptr, b->stream));
     LB_BCUDA(b, cudaMemcpyAsync(rho, b->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     return batch_sync(b);
@@ -515,8 +536,8 @@ lb_status lb_batch_get_populations(lb_batch *b, int i, void *dst, size_t bytes) 
     if (bytes != 9 * (size_t)g.ny * row) return bfail(b, LB_EINVAL, "size mismatch");
     // the spare buffer of lattice i receives the pulled populations in the host layout
     // (free between steps), then one contiguous copy
-    void *spare = buf(b, i, b->phase ^ 1);
-    LB_BCUDA(b, lbm::launch_stream(b->prec, g, buf(b, i, b->phase), spare, true, b->stream));
+    void *spare = buf(b, i, cur(b, i) ^ 1);
+    LB_BCUDA(b, lbm::launch_stream(b->prec, g, buf(b, i, cur(b, i)), spare, true, b->stream));
     LB_BCUDA(b, cudaMemcpyAsync(dst, spare, bytes, cudaMemcpyDeviceToHost, b->stream));
     return batch_sync(b);
 }
@@ -540,6 +561,22 @@ lb_status lb_batch_measure(lb_batch *b, const double *radius, double *out) {
         lbm::droplet_results(&raw[8 * (size_t)i], (double)b->geom[i].nx * b->geom[i].ny,
                              errs[i] != 0, out + 8 * (size_t)i);
     return LB_OK;
+}
+
+lb_status lb_batch_set_active(lb_batch *b, const unsigned char *active) {
+    if (!b || !active) return LB_EINVAL;
+    if (b->sticky != LB_OK) return b->sticky;
+    if (b->steps & 1)
+        return bfail(b, LB_EINVAL, "lb_batch_set_active: call at an even step count");
+    LB_BCUDA(b, cudaStreamSynchronize(b->stream));   // no queued step reads the old items
+    for (int i = 0; i < b->n; ++i) b->active[i] = active[i] ? 1 : 0;
+    lb_status s = b->prec == LB_FP32 ? upload_lattices<float>(b) : upload_lattices<double>(b);
+    if (s != LB_OK) return s;
+    return apply_batch_launch(b, b->variant, b->rows);
+}
+
+long long lb_batch_lattice_steps(const lb_batch *b, int i) {
+    return (b && i >= 0 && i < b->n) ? b->lat_steps[i] : -1;
 }
 
 long long lb_batch_steps_done(const lb_batch *b) { return b ? b->steps : 0; }

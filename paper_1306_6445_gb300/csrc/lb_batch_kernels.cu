@@ -18,7 +18,7 @@ k_batch_measure(const BatchLattice<T> *__restrict__ lats, int phase,
     const BatchLattice<T> &L = lats[blockIdx.x];
     const DevConsts<T> P = L.P;
     const int nx = L.nx, ny = L.ny;
-    const T *g = L.g[phase];
+    const T *g = L.g[L.frozen ? 0 : phase];
     const double R = radius[blockIdx.x];
     const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1);
     const double r_in = 0.5 * R, r_out = R + 0.3 * 0.5 * min(nx, ny);

@@ -51,6 +51,7 @@ struct BatchLattice {
     DevConsts<T> P;
     int nx, ny, pitch;
     unsigned plane;
+    int frozen;           // 1: set inactive (not stepped); its state stays in g[0]
 };
 
 template <typename T>

@@ -38,6 +38,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
             "lb_batch_steps_done", "lb_batch_size", "lb_batch_last_error", "lb_batch_free",
+            "lb_batch_set_active", "lb_batch_lattice_steps",
             "lb_strip_widths",
             # include/lb_mlp.h
             "lb_mlp_create", "lb_mlp_set_params", "lb_mlp_get_params", "lb_mlp_set_data",
@@ -135,6 +136,8 @@ def load_library():
         "lb_batch_set_launch": (I, [P, I, I]),
         "lb_batch_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_batch_steps_done": (C.c_longlong, [P]),
+        "lb_batch_set_active": (I, [P, C.POINTER(C.c_ubyte)]),
+        "lb_batch_lattice_steps": (C.c_longlong, [P, I]),
         "lb_batch_size": (I, [P]),
         "lb_batch_last_error": (C.c_char_p, [P]),
         "lb_batch_free": (None, [P]),
@@ -634,6 +637,17 @@ class Batch:
     @property
     def steps_done(self) -> int:
         return int(load_library().lb_batch_steps_done(self.b))
+
+    def set_active(self, active):
+        """Which lattices lb_batch_step advances (a boolean per lattice); see include/lb.h."""
+        a = np.ascontiguousarray(np.asarray(active, dtype=bool), dtype=np.uint8)
+        if a.shape != (self.n,):
+            raise LBError(LB_EINVAL, "set_active", f"need {self.n} flags")
+        _bcheck(load_library().lb_batch_set_active(self.b, a.ctypes.data_as(C.POINTER(C.c_ubyte))),
+                "lb_batch_set_active", self.b)
+
+    def lattice_steps(self, i: int) -> int:
+        return int(load_library().lb_batch_lattice_steps(self.b, int(i)))
 
     def close(self):
         if getattr(self, "b", None):

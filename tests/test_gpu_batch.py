@@ -159,3 +159,61 @@ def test_a_failing_lattice_is_flagged_and_the_others_continue(lbm):
     m = b.measure(radii)
     assert m[2, 7] == 1 and not m[np.arange(len(descs)) != 2, 7].any()
     b.close()
+
+
+def single_run(lbm, d, rho, steps, prec="fp32"):
+    lat = lbm.Lattice(d.nx, d.ny, d.eos, d.G, kappa=d.kappa, sigma_force=d.sigma_force,
+                      rates=d.rates, prec=prec)
+    lat.set_rho_u(rho)
+    lat.step(steps)
+    out = lat.populations()
+    lat.close()
+    return out
+
+
+def test_inactive_lattices_keep_their_state_and_can_resume(lbm):
+    """lb_batch_set_active: an inactive lattice is not advanced, keeps its state (readable
+    and measurable at any step count), and continues like a lattice that was never
+    stopped once made active again; the active ones are unaffected."""
+    descs, rhos, radii = small_batch(lbm)
+    b = lbm.Batch(descs, prec="fp32")
+    for i, r in enumerate(rhos):
+        b.set_rho_u(i, r)
+    b.step(64)
+    frozen = [1, 4]
+    snap = {i: b.populations(i) for i in frozen}
+    m_before = b.measure(radii)
+    active = np.ones(len(descs), dtype=bool)
+    active[frozen] = False
+    b.set_active(active)
+    b.step(64 + 3)                       # graph replay, then direct launches: odd count
+    assert b.steps_done == 131
+    for i in range(len(descs)):
+        assert b.lattice_steps(i) == (64 if i in frozen else 131)
+    # readable and measurable while the batch's step count is odd
+    m_odd = b.measure(radii)
+    for i in frozen:
+        assert np.array_equal(b.populations(i), snap[i])
+        assert np.array_equal(m_odd[i], m_before[i])
+    for i in range(len(descs)):
+        if i not in frozen:
+            assert np.array_equal(b.populations(i), single_run(lbm, descs[i], rhos[i], 131)), i
+    # changing the set at an odd step count is refused and changes nothing
+    with pytest.raises(lbm.LBError) as ei:
+        b.set_active(np.ones(len(descs), dtype=bool))
+    assert ei.value.status == lbm.LB_EINVAL
+    b.step(1)                            # even again
+    b.set_active(np.ones(len(descs), dtype=bool))
+    b.step(64)
+    for i in frozen:                     # 64 + 64 steps in all, as if never stopped
+        assert b.lattice_steps(i) == 128
+        assert np.array_equal(b.populations(i), single_run(lbm, descs[i], rhos[i], 128)), i
+    # no active lattice: stepping is a no-op
+    b.set_active(np.zeros(len(descs), dtype=bool))
+    before = [b.populations(i) for i in range(len(descs))]
+    b.step(70)
+    b.sync()
+    for i in range(len(descs)):
+        assert np.array_equal(b.populations(i), before[i])
+    assert not b.errors().any()
+    b.close()

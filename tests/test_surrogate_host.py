@@ -8,7 +8,7 @@ ln sigma against ln(1 - kappa), otherwise; and failed runs."""
 import numpy as np
 import pytest
 
-from paper_1306_6445_gb300 import surrogate
+from paper_1306_6445_gb300 import surrogate, sweep
 
 
 P_EXP = 1.15
@@ -97,3 +97,66 @@ def test_failed_runs_stay_failed_and_are_reported(monkeypatch):
     t, tau, s, k = targets()
     r = surrogate.tune_kappa(None, FakeNet(), t, tau, s, tol=0.02, max_rounds=2)
     assert np.all(np.isnan(r["sigma"])) and np.all(np.isnan(r["rel_err"]))
+
+
+# ---- the converged sweep protocol (sweep.converged_readings) against a fake batch ------
+
+class FakeBatch:
+    """Stands in for lbm.Batch: lattice i reads theta_i(t) = target_i (1 + a_i cos(t / 50)
+    exp(-t / tau_i)); set_active must come at even step counts, like the library's."""
+
+    def __init__(self, target, amp, tau):
+        self.target, self.amp, self.tau = map(np.asarray, (target, amp, tau))
+        self.n = len(self.target)
+        self.t = np.zeros(self.n)
+        self.active = np.ones(self.n, dtype=bool)
+        self.steps = 0
+        self.calls = []
+
+    def step(self, k):
+        assert k > 0
+        self.t[self.active] += k
+        self.steps += k
+
+    def measure(self, radii):
+        th = self.target * (1 + self.amp * np.cos(self.t / 50.0) * np.exp(-self.t / self.tau))
+        out = np.zeros((self.n, 8))
+        out[:, 0], out[:, 1], out[:, 2] = th, 0.3, 0.02
+        return out
+
+    def set_active(self, active):
+        assert self.steps % 2 == 0
+        self.active = np.asarray(active, dtype=bool).copy()
+        self.calls.append((self.steps, self.active.copy()))
+
+
+def test_step_budget_grows_with_the_square_of_the_side():
+    assert sweep.step_budget(64) == 8192                    # the floor
+    assert sweep.step_budget(512) == 131072                 # 0.5 * 512^2
+    assert sweep.step_budget(384) % sweep.WINDOW == 0 and sweep.step_budget(384) >= 73728
+
+
+def test_converged_readings_retires_each_lattice_at_its_budget():
+    budgets = np.array([8192, 16384, 8192, 32768])
+    b = FakeBatch(target=[1e-3, 2e-3, 3e-3, 4e-3], amp=[0.5, 0.5, 0.5, 0.5],
+                  tau=[500.0, 500.0, 1e9, 500.0])
+    r = sweep.converged_readings(b, budgets, np.ones(4))
+    # every lattice took exactly its budget and the batch stopped with the last one
+    assert np.array_equal(b.t, budgets) and b.steps == budgets.max()
+    # retirements at the budgets, in order
+    assert [c[0] for c in b.calls] == [8192, 16384, 32768]
+    # damped lattices read their target; the undamped one (tau = inf) oscillates between
+    # windows and is not converged
+    ok = [0, 1, 3]
+    assert np.allclose(r["theta"][ok], b.target[ok], rtol=1e-6)
+    assert r["converged"][ok].all() and not r["converged"][2]
+    # the reading is the mean over the last window (32 readings of the fake's curve)
+    ts = np.arange(8192 - 2048 + 64, 8192 + 1, 64)
+    want = np.mean(3e-3 * (1 + 0.5 * np.cos(ts / 50.0) * np.exp(-ts / 1e9)))
+    assert r["theta"][2] == pytest.approx(want, rel=1e-12)
+
+
+def test_converged_readings_rejects_budgets_off_the_window():
+    b = FakeBatch([1.0], [0.0], [1.0])
+    with pytest.raises(ValueError):
+        sweep.converged_readings(b, [5000], [1.0])
