@@ -115,6 +115,15 @@ def profiled_value(name: str, key: str, prec: str):
     return float(m_v.group(1))
 
 
+def profiled_kernel(prec: str):
+    """The kernel named by the committed 2048^2 summary (`kernel: name`), or None."""
+    path = os.path.join(ROOT, "profiles", f"fused_step_{prec}_2048sq.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"^kernel:\s*(\S+)", open(path).read(), re.M)
+    return m.group(1) if m else None
+
+
 def profiled_traffic(prec: str):
     """DRAM bytes per fused-step launch of the 2048^2 workload from the committed ncu summary."""
     return profiled_value(f"fused_step_{prec}_2048sq", "dram_bytes_per_launch", prec)
@@ -687,10 +696,12 @@ def native(args):
     hbm, peak_src = measured_peaks()
     alg = ALG_BYTES_PER_SITE["fp32"] * sites
     achieved = alg / (kern_ms * 1e-3) / 1e9
-    traffic = profiled_traffic("fp32")
+    kname = "k_pull_collide_stage<float>" if shape["variant"] >= 4 else "k_pull_collide<float>"
+    # the committed capture counts only for the kernel it was taken on
+    traffic = profiled_traffic("fp32") if profiled_kernel("fp32") == kname else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic,
-            "kernel": "k_pull_collide<float>", "launch": shape, "alg_bytes_per_launch": alg,
+            "kernel": kname, "launch": shape, "alg_bytes_per_launch": alg,
             "kernel_ms": round(kern_ms, 5), "peak_source": f"{peak_src} (copy bandwidth)"}
 
     # FP64 leg
