@@ -144,6 +144,17 @@ lb_status lb_set_viscosity_switch(lb_ctx *ctx, double rho_1, double s_v_vapour);
  * context that is not LB_BF16 or a non-finite rho_s. */
 lb_status lb_set_storage_shift(lb_ctx *ctx, double rho_s);
 
+/* Rounding of the values an LB_BF16 step stores (f_a - w_a rho_s, FP32, to BF16).
+ * LB_ROUND_NEAREST (the default): round to nearest even. LB_ROUND_STOCHASTIC: the magnitude
+ * rounds up with probability (dropped bits) / 2^16, so each stored value is unbiased; the
+ * random bits come from a counter-based generator (MurmurHash3's 32-bit finaliser) keyed by
+ * the site, the step count and the population, so runs are reproducible and do not depend
+ * on the launch variant. The initial state of lb_set_rho_u is rounded to nearest. Library
+ * plumbing for the precision study (the paper has no counterpart). Synchronises.
+ * Errors: LB_EINVAL for a context that is not LB_BF16 or an unknown mode. */
+enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
+lb_status lb_set_storage_rounding(lb_ctx *ctx, int mode);
+
 /* Choose the step kernel's variant (0 .. lb_launch_variants()-1) and the number of rows
  * each CTA marches over (rows = 0: about three waves of resident CTAs, at least 8 rows).
  * Synchronises the stream. Errors: LB_EINVAL for an unknown variant or rows < 0. */

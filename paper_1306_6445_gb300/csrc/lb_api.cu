@@ -496,6 +496,17 @@ lb_status lb_set_storage_shift(lb_ctx *c, double rho_s) {
     return LB_OK;
 }
 
+lb_status lb_set_storage_rounding(lb_ctx *c, int mode) {
+    lb_status s = check_usable(c);
+    if (s != LB_OK) return s;
+    if (c->prec != LB_BF16) return fail(c, LB_EINVAL, "lb_set_storage_rounding: LB_BF16 contexts only");
+    if (mode != LB_ROUND_NEAREST && mode != LB_ROUND_STOCHASTIC)
+        return fail(c, LB_EINVAL, "lb_set_storage_rounding: unknown mode");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->consts.stochastic = mode == LB_ROUND_STOCHASTIC ? 1 : 0;
+    return LB_OK;
+}
+
 lb_status lb_debug_stall_row(lb_ctx *c, int row) {
     lb_status s = check_usable(c);
     if (s != LB_OK) return s;
@@ -536,6 +547,7 @@ lb_status lb_step(lb_ctx *c, int n) {
     for (int i = 0; i < n; ++i) {
         // alternate the visiting order: each step first reads the rows the previous one
         // wrote last (still in L2 when the state is not much larger than L2)
+        c->consts.step_key = (unsigned)c->steps;   // the stochastic-rounding counter
         LB_CUDA(c, lbm::launch_step(c->prec, c->consts, c->geom, c->launch, (int)(c->steps & 1),
                                     &c->tmap[c->cur], c->f[c->cur ^ 1], c->d_err, c->stream));
         c->cur ^= 1;

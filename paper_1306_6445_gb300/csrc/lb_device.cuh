@@ -42,6 +42,9 @@ struct DevConsts {
     // s_vV; the Eq. 17 coefficients for that rate
     T rho_sw, s_vV, v_keep_V, v_half_V, v_src_V;
     int stall_row;
+    // LB_BF16 stochastic rounding: on/off and the step of the launch (the counter)
+    int sr_on;
+    unsigned sr_step;
 };
 
 // Per-lattice record of the batched step (lives in a device table).
@@ -76,6 +79,8 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.v_half_V = T(1.0 - 0.5 * c.s_v_vapour);
     d.v_src_V = T(-c.s_v_vapour);
     d.stall_row = c.stall_row;
+    d.sr_on = c.stochastic;
+    d.sr_step = c.step_key;
     return d;
 }
 
@@ -108,12 +113,48 @@ __device__ __forceinline__ float pop_dec<__nv_bfloat16>(__nv_bfloat16 v, int a,
                                                          const DevConsts<float> &P) {
     return __fadd_rn(__bfloat162float(v), P.wshift[a]);
 }
+// MurmurHash3's 32-bit finaliser (fmix32; A. Appleby, public domain): a bijective mix of a
+// 32-bit counter into well-spread bits, the generator of the stochastic rounding below.
+__device__ __forceinline__ unsigned mix32(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// The counter of a site pair (first column x, row y) in the step of the launch, and the 32
+// random bits of its population a (16 per site of the pair): reproducible, and independent
+// of the launch shape.
+__device__ __forceinline__ unsigned sr_pair_key(int x, int y, unsigned step) {
+    return mix32(mix32((unsigned)y * 0x9e3779b1u + (unsigned)x) ^ (step * 0x85ebca6bu));
+}
+__device__ __forceinline__ unsigned sr_bits(unsigned key, int a) {
+    return mix32(key + (unsigned)(a + 1) * 0x9e3779b9u);
+}
+
+// BF16 of v rounded stochastically with the 16 random bits r16: r16 is added below the
+// kept bits and the rest cut off, so the magnitude rounds up with probability (dropped
+// bits) / 2^16 and the expected stored value is v.
+__device__ __forceinline__ __nv_bfloat16 bf16_stochastic(float v, unsigned r16) {
+    unsigned b = __float_as_uint(v);
+    if ((b & 0x7f800000u) != 0x7f800000u) b += r16 & 0xffffu;   // not Inf / NaN
+    __nv_bfloat16_raw raw;
+    raw.x = (unsigned short)(b >> 16);
+    return __nv_bfloat16(raw);
+}
+
+// r16: the random bits of the stochastic rounding (LB_BF16 with it on), else unused
 template <typename T>
-__device__ __forceinline__ T pop_enc(Arith<T> v, int, const DevConsts<Arith<T>> &) { return v; }
+__device__ __forceinline__ T pop_enc(Arith<T> v, int, const DevConsts<Arith<T>> &,
+                                     unsigned = 0) { return v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 pop_enc<__nv_bfloat16>(float v, int a,
-                                                                 const DevConsts<float> &P) {
-    return __float2bfloat16_rn(__fsub_rn(v, P.wshift[a]));
+                                                                 const DevConsts<float> &P,
+                                                                 unsigned r16) {
+    const float d = __fsub_rn(v, P.wshift[a]);
+    return P.sr_on ? bf16_stochastic(d, r16) : __float2bfloat16_rn(d);
 }
 
 // Interaction potential psi(rho) (Sec. II): psi0 exp(-rho0/rho), or

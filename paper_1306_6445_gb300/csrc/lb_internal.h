@@ -58,6 +58,8 @@ struct Consts {
     double s_e, s_z, s_q, s_v;  // non-conserved relaxation rates (s_rho, s_j drop out, see kernels)
     int stall_row;  // test hook: the step kernel never requests this ring row (INT_MIN = off)
     double shift_rho;  // rho_s of the LB_BF16 storage shift f_a - w_a rho_s (0 otherwise)
+    int stochastic;    // LB_BF16: 1 = stochastic rounding of the stored values (0 = nearest)
+    unsigned step_key; // the step a launch takes (the stochastic-rounding counter)
     // nu(rho) of the open-boundary kernels: s_v_vapour where rho < rho_sw (-inf: off)
     double rho_sw, s_v_vapour;
 };

@@ -495,10 +495,13 @@ cudaError_t launch_stream(int prec, const Geom &g, const void *gbuf, void *f, bo
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_feq(int prec, const Consts &c, const Geom &g, const double *rho,
+cudaError_t launch_init_feq(int prec, const Consts &c_in, const Geom &g, const double *rho,
                             const double *ux, const double *uy, void *f, int *err,
                             cudaStream_t st) {
     const unsigned nb = blocks_for((long long)g.nx * g.ny, 256);
+    Consts c = c_in;
+    c.stochastic = 0;   // the initial state is rounded to nearest
+
 #define LB_INIT(T, EOSK)                                                                   \
     k_init_feq<T, EOSK><<<nb, 256, 0, st>>>(rho, ux, uy, static_cast<T *>(f),               \
                                             to_dev<Arith<T>>(c),                             \

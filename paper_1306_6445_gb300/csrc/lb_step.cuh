@@ -301,17 +301,40 @@ __device__ __forceinline__ void store_pair<double>(double *p, V2<double> v, bool
     else p[0] = v.x;
 }
 
-// stored pair of population a (encoded from its value)
+// stored pair of population a (encoded from its value); r32: the stochastic-rounding bits
+// of the pair (low half for the first site, high half for the second), LB_BF16 only
 template <typename T>
 __device__ __forceinline__ void store_pop_pair(T *p, V2<Arith<T>> v, bool both, int a,
-                                               const DevConsts<Arith<T>> &P) {
+                                               const DevConsts<Arith<T>> &P, unsigned r32 = 0) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
         const V2<float> d = v - V2<float>::all(P.wshift[a]);   // lane-wise as pop_enc
-        if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(d.v);
-        else p[0] = __float2bfloat16_rn(d.lo());
+        if (P.sr_on) {
+            const __nv_bfloat16 lo = bf16_stochastic(d.lo(), r32), hi = bf16_stochastic(d.hi(), r32 >> 16);
+            if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(lo, hi);
+            else p[0] = lo;
+        } else {
+            if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(d.v);
+            else p[0] = __float2bfloat16_rn(d.lo());
+        }
     } else {
         store_pair<T>(p, v, both);
     }
+}
+
+// the stochastic-rounding key of a site pair (LB_BF16 with stochastic rounding), else 0
+template <typename T>
+__device__ __forceinline__ unsigned store_key(int x, int y, const DevConsts<Arith<T>> &P) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        return P.sr_on ? sr_pair_key(x, y, P.sr_step) : 0u;
+    else
+        return 0u;
+}
+template <typename T>
+__device__ __forceinline__ unsigned store_bits(unsigned key, int a, const DevConsts<Arith<T>> &P) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        return P.sr_on ? sr_bits(key, a) : 0u;
+    else
+        return 0u;
 }
 
 __device__ __forceinline__ void grid_dependency_wait() {
@@ -490,16 +513,19 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH<T>);
+            const unsigned key = store_key<T>(x, yr, P);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
-                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
+                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
+                                  store_bits<T>(key, a, P));
             if (BC == 2) {
                 // open sides: the ghost columns repeat the edge columns (zero gradient)
                 if (x == 0 || x + 1 >= nx - 1) {
                     const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
-                        const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                        const unsigned r = store_bits<T>(key, a, P);
+                        const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -511,7 +537,8 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                 const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                    const unsigned r = store_bits<T>(key, a, P);
+                    const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
@@ -765,21 +792,25 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH<T>);
+            const unsigned key = store_key<T>(x, y, P);
             if (w == TX) {   // a whole strip (CTA-uniform): every thread stores two sites
 #pragma unroll
                 for (int a = 0; a < 9; ++a)
-                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], true, a, P);
+                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], true, a, P,
+                                      store_bits<T>(key, a, P));
             } else {
 #pragma unroll
                 for (int a = 0; a < 9; ++a)
-                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P);
+                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
+                                      store_bits<T>(key, a, P));
             }
             if (BC == 2) {
                 if (x == 0 || x + 1 >= nx - 1) {
                     const unsigned rowi = (unsigned)y * (unsigned)pitch;
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
-                        const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                        const unsigned r = store_bits<T>(key, a, P);
+                        const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -790,7 +821,8 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
                 const unsigned rowi = (unsigned)y * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    const T v0 = pop_enc<T>(fc[a].lo(), a, P), v1 = pop_enc<T>(fc[a].hi(), a, P);
+                    const unsigned r = store_bits<T>(key, a, P);
+                    const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;

@@ -34,6 +34,7 @@ EXPORTED = ["lb_pitch", "lb_buffer_bytes", "lb_init", "lb_init_ex", "lb_set_rho_
             "lb_probe_fp64_fma_rate", "lb_measure_droplet", "lb_interface_height",
             "lb_set_launch", "lb_get_launch", "lb_debug_stall_row", "lb_reduce_noalloc",
             "lb_autotune", "lb_set_storage_shift", "lb_set_viscosity_switch",
+            "lb_set_storage_rounding",
             "lb_batch_create", "lb_batch_set_rho_u", "lb_batch_step", "lb_batch_sync",
             "lb_batch_errors", "lb_batch_get_rho", "lb_batch_get_populations", "lb_batch_measure",
             "lb_batch_autotune", "lb_batch_set_launch", "lb_batch_get_launch",
@@ -120,6 +121,7 @@ def load_library():
         "lb_set_launch": (I, [P, I, I]),
         "lb_autotune": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
         "lb_set_storage_shift": (I, [P, D]),
+        "lb_set_storage_rounding": (I, [P, I]),
         "lb_set_viscosity_switch": (I, [P, D, D]),
         "lb_get_launch": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "lb_debug_stall_row": (I, [P, I]),
@@ -376,6 +378,13 @@ def lb_set_viscosity_switch(ctx, rho_1: float, s_v_vapour: float):
            "lb_set_viscosity_switch", ctx)
 
 
+LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = 0, 1
+
+
+def lb_set_storage_rounding(ctx, mode: int):
+    _check(load_library().lb_set_storage_rounding(ctx, int(mode)), "lb_set_storage_rounding", ctx)
+
+
 def lb_set_storage_shift(ctx, rho_s: float):
     _check(load_library().lb_set_storage_shift(ctx, float(rho_s)), "lb_set_storage_shift", ctx)
 
@@ -428,6 +437,7 @@ class Lattice:
     walls_y: bool = False
     buffers: str = "torch"
     storage_shift: float = 0.0   # rho_s of prec="bf16" (stored BF16 of f_a - w_a rho_s)
+    stochastic_rounding: bool = False   # prec="bf16": LB_ROUND_STOCHASTIC
     open_bc: bool = False         # LB_BC_OPEN: wall below, open top and sides (Sec. V.C)
     viscosity_switch: tuple = None   # (rho_1, s_v where rho < rho_1), LB_BC_OPEN only
 
@@ -457,6 +467,8 @@ class Lattice:
                                self.rates, self._prec, bc, None)
         if self._prec == LB_BF16:
             lb_set_storage_shift(self.ctx, self.storage_shift)
+            if self.stochastic_rounding:
+                lb_set_storage_rounding(self.ctx, LB_ROUND_STOCHASTIC)
         if self.viscosity_switch is not None:
             lb_set_viscosity_switch(self.ctx, *self.viscosity_switch)
 

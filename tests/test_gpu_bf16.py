@@ -170,3 +170,66 @@ def test_error_table_against_fp64(lbm):
     assert rows["fp32"]["ratio"] == pytest.approx(ref["ratio"], rel=5e-3)
     assert rows["fp32"]["theta"] == pytest.approx(ref["theta"], rel=5e-3)
     assert all(np.isfinite(v) for v in rows["bf16"].values())
+
+
+# ---- stochastic rounding (lb_set_storage_rounding) --------------------------------------
+
+def stochastic_case(lbm, walls, variant=None, rs=0.0, seed=21):
+    eos = lbm.cs_eos(0.8)
+    rates = lbm.RateParams.from_viscosity(0.1)
+    rv, rl, _ = lbm.lb_maxwell(eos, -1.0)
+    rng = np.random.default_rng(seed)
+    nx, ny = 203, 77
+    rho = I.smooth_random_density(rng, nx, ny, rv * 1.2, rl * 0.9)
+    f0 = I.random_populations(rng, rho)
+    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=0.4, sigma_force=0.05, rates=rates, prec="bf16",
+                      walls_y=walls, storage_shift=rs, stochastic_rounding=True)
+    if variant is not None:
+        lbm.lb_set_launch(lat.ctx, *variant)
+    b0 = encode(f0, rs)
+    lat.set_populations(b0)
+    lat.step(1)
+    out = lat.populations()
+    lat.close()
+    ref = OL.step(decode(b0, rs).astype(np.float64),
+                  oracle_params(eos, -1.0, 0.4, 0.05, rates, walls))
+    return out, ref
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_stochastic_rounding_stays_within_one_spacing_and_is_reproducible(lbm, walls):
+    """Each stored value is one of the two BF16 neighbours of the FP32 result, so a step is
+    within one spacing of the oracle as with nearest rounding; the random bits depend only
+    on site, step and population, so repeated runs and every launch variant give the same
+    bits."""
+    rs = 0.05
+    out, ref = stochastic_case(lbm, walls, rs=rs)
+    got = decode(out, rs).astype(np.float64)
+    assert np.all(np.abs(got - ref) <= one_step_bound(ref, rs))
+    again, _ = stochastic_case(lbm, walls, rs=rs)
+    assert np.array_equal(out, again)
+    for v in range(lbm.lb_launch_variants()):
+        other, _ = stochastic_case(lbm, walls, variant=(v, 13), rs=rs)
+        assert np.array_equal(out, other), v
+
+
+def test_stochastic_rounding_is_unbiased(lbm):
+    """The rounding error of stochastic rounding has zero mean: over the 15 631 sites of a
+    step its mean for every population stays within 5 standard errors (the error of one
+    value is at most one spacing, its variance at most spacing^2 / 4)."""
+    out, ref = stochastic_case(lbm, False, rs=0.0, seed=5)
+    got = decode(out, 0.0).astype(np.float64)
+    err = got - ref
+    spacing = 2.0 ** (np.floor(np.log2(np.abs(ref))) - 7)
+    n = err[0].size
+    for a in range(9):
+        se = np.sqrt(np.mean(spacing[a] ** 2) / 4.0 / n)
+        assert abs(err[a].mean()) < 5.0 * se, (a, err[a].mean(), se)
+
+
+def test_stochastic_rounding_rejects_other_precisions(lbm):
+    lat = lbm.Lattice(32, 32, lbm.cs_eos(0.8), -1.0, prec="fp32")
+    with pytest.raises(lbm.LBError) as ei:
+        lbm.lb_set_storage_rounding(lat.ctx, lbm.LB_ROUND_STOCHASTIC)
+    assert ei.value.status == lbm.LB_EINVAL
+    lat.close()
