@@ -42,8 +42,7 @@ struct DevConsts {
     // s_vV; the Eq. 17 coefficients for that rate
     T rho_sw, s_vV, v_keep_V, v_half_V, v_src_V;
     int stall_row;
-    // LB_BF16 stochastic rounding: on/off and the step of the launch (the counter)
-    int sr_on;
+    // LB_BF16 stochastic rounding: the step of the launch (the counter)
     unsigned sr_step;
 };
 
@@ -79,7 +78,6 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.v_half_V = T(1.0 - 0.5 * c.s_v_vapour);
     d.v_src_V = T(-c.s_v_vapour);
     d.stall_row = c.stall_row;
-    d.sr_on = c.stochastic;
     d.sr_step = c.step_key;
     return d;
 }
@@ -145,16 +143,18 @@ __device__ __forceinline__ __nv_bfloat16 bf16_stochastic(float v, unsigned r16) 
     return __nv_bfloat16(raw);
 }
 
-// r16: the random bits of the stochastic rounding (LB_BF16 with it on), else unused
-template <typename T>
-__device__ __forceinline__ T pop_enc(Arith<T> v, int, const DevConsts<Arith<T>> &,
-                                     unsigned = 0) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 pop_enc<__nv_bfloat16>(float v, int a,
-                                                                 const DevConsts<float> &P,
-                                                                 unsigned r16) {
-    const float d = __fsub_rn(v, P.wshift[a]);
-    return P.sr_on ? bf16_stochastic(d, r16) : __float2bfloat16_rn(d);
+// SR: LB_BF16 with stochastic rounding, r16 its random bits; otherwise nearest even
+template <typename T, bool SR = false>
+__device__ __forceinline__ T pop_enc(Arith<T> v, int a, const DevConsts<Arith<T>> &P,
+                                     unsigned r16 = 0) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        const float d = __fsub_rn(v, P.wshift[a]);
+        if constexpr (SR) return bf16_stochastic(d, r16);
+        else return __float2bfloat16_rn(d);
+    } else {
+        (void)a; (void)P; (void)r16;
+        return v;
+    }
 }
 
 // Interaction potential psi(rho) (Sec. II): psi0 exp(-rho0/rho), or

@@ -499,8 +499,7 @@ cudaError_t launch_init_feq(int prec, const Consts &c_in, const Geom &g, const d
                             const double *ux, const double *uy, void *f, int *err,
                             cudaStream_t st) {
     const unsigned nb = blocks_for((long long)g.nx * g.ny, 256);
-    Consts c = c_in;
-    c.stochastic = 0;   // the initial state is rounded to nearest
+    const Consts &c = c_in;   // the initial state is rounded to nearest (pop_enc default)
 
 #define LB_INIT(T, EOSK)                                                                   \
     k_init_feq<T, EOSK><<<nb, 256, 0, st>>>(rho, ux, uy, static_cast<T *>(f),               \

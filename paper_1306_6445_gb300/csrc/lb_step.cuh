@@ -301,14 +301,15 @@ __device__ __forceinline__ void store_pair<double>(double *p, V2<double> v, bool
     else p[0] = v.x;
 }
 
-// stored pair of population a (encoded from its value); r32: the stochastic-rounding bits
-// of the pair (low half for the first site, high half for the second), LB_BF16 only
-template <typename T>
+// stored pair of population a (encoded from its value); SR: LB_BF16 with stochastic
+// rounding, r32 its random bits for the pair (low half for the first site, high half for
+// the second)
+template <typename T, bool SR = false>
 __device__ __forceinline__ void store_pop_pair(T *p, V2<Arith<T>> v, bool both, int a,
                                                const DevConsts<Arith<T>> &P, unsigned r32 = 0) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
         const V2<float> d = v - V2<float>::all(P.wshift[a]);   // lane-wise as pop_enc
-        if (P.sr_on) {
+        if constexpr (SR) {
             const __nv_bfloat16 lo = bf16_stochastic(d.lo(), r32), hi = bf16_stochastic(d.hi(), r32 >> 16);
             if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(lo, hi);
             else p[0] = lo;
@@ -321,18 +322,18 @@ __device__ __forceinline__ void store_pop_pair(T *p, V2<Arith<T>> v, bool both, 
     }
 }
 
-// the stochastic-rounding key of a site pair (LB_BF16 with stochastic rounding), else 0
-template <typename T>
+// the stochastic-rounding key of a site pair (SR: LB_BF16 with stochastic rounding), else 0
+template <typename T, bool SR>
 __device__ __forceinline__ unsigned store_key(int x, int y, const DevConsts<Arith<T>> &P) {
-    if constexpr (std::is_same<T, __nv_bfloat16>::value)
-        return P.sr_on ? sr_pair_key(x, y, P.sr_step) : 0u;
+    if constexpr (SR && std::is_same<T, __nv_bfloat16>::value)
+        return sr_pair_key(x, y, P.sr_step);
     else
         return 0u;
 }
-template <typename T>
-__device__ __forceinline__ unsigned store_bits(unsigned key, int a, const DevConsts<Arith<T>> &P) {
-    if constexpr (std::is_same<T, __nv_bfloat16>::value)
-        return P.sr_on ? sr_bits(key, a) : 0u;
+template <typename T, bool SR>
+__device__ __forceinline__ unsigned store_bits(unsigned key, int a, const DevConsts<Arith<T>> &) {
+    if constexpr (SR && std::is_same<T, __nv_bfloat16>::value)
+        return sr_bits(key, a);
     else
         return 0u;
 }
@@ -365,7 +366,7 @@ __device__ __forceinline__ void grid_dependents_launch() {
 // The caller has initialised the S ring mbarriers (fresh, phase 0) and waited for the
 // previous grid. Returns 0, or ERR_TIMEOUT after a bounded wait gave up (then every copy
 // still in flight has landed, or its own bounded wait gave up too).
-template <typename T, int EOS, int BC, int TX, int S, int G>
+template <typename T, int EOS, int BC, int TX, int S, int G, bool SR = false>
 __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ gout,
                                      const DevConsts<Arith<T>> &P, const int nx, const int ny,
                                      const int pitch, const unsigned plane, const int x0,
@@ -513,19 +514,19 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH<T>);
-            const unsigned key = store_key<T>(x, yr, P);
+            const unsigned key = store_key<T, SR>(x, yr, P);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
-                store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
-                                  store_bits<T>(key, a, P));
+                store_pop_pair<T, SR>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
+                                  store_bits<T, SR>(key, a, P));
             if (BC == 2) {
                 // open sides: the ghost columns repeat the edge columns (zero gradient)
                 if (x == 0 || x + 1 >= nx - 1) {
                     const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
-                        const unsigned r = store_bits<T>(key, a, P);
-                        const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
+                        const unsigned r = store_bits<T, SR>(key, a, P);
+                        const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -537,8 +538,8 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                 const unsigned rowi = (unsigned)yr * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    const unsigned r = store_bits<T>(key, a, P);
-                    const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
+                    const unsigned r = store_bits<T, SR>(key, a, P);
+                    const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
@@ -643,7 +644,7 @@ __device__ __forceinline__ void pull_stage(V2<Arith<T>> (&f)[9], const T *stg, i
 // from stage i (slot i mod S). Iteration k waits for stage k + 2, forms psi of row
 // P_{k+2} (keeping its populations for the next collision), passes a barrier, lets thread
 // 0 request stages up to k + 2 + S into the freed slots, then collides row start + k dir.
-template <typename T, int EOS, int BC, int TX, int S>
+template <typename T, int EOS, int BC, int TX, int S, bool SR = false>
 __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restrict__ gout,
                                            const DevConsts<Arith<T>> &P, const int nx,
                                            const int ny, const int pitch, const unsigned plane,
@@ -792,25 +793,25 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH<T>);
-            const unsigned key = store_key<T>(x, y, P);
+            const unsigned key = store_key<T, SR>(x, y, P);
             if (w == TX) {   // a whole strip (CTA-uniform): every thread stores two sites
 #pragma unroll
                 for (int a = 0; a < 9; ++a)
-                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], true, a, P,
-                                      store_bits<T>(key, a, P));
+                    store_pop_pair<T, SR>(gout + (idx + plane_of(a) * plane), fc[a], true, a, P,
+                                      store_bits<T, SR>(key, a, P));
             } else {
 #pragma unroll
                 for (int a = 0; a < 9; ++a)
-                    store_pop_pair<T>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
-                                      store_bits<T>(key, a, P));
+                    store_pop_pair<T, SR>(gout + (idx + plane_of(a) * plane), fc[a], both, a, P,
+                                      store_bits<T, SR>(key, a, P));
             }
             if (BC == 2) {
                 if (x == 0 || x + 1 >= nx - 1) {
                     const unsigned rowi = (unsigned)y * (unsigned)pitch;
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
-                        const unsigned r = store_bits<T>(key, a, P);
-                        const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
+                        const unsigned r = store_bits<T, SR>(key, a, P);
+                        const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -821,8 +822,8 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
                 const unsigned rowi = (unsigned)y * (unsigned)pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    const unsigned r = store_bits<T>(key, a, P);
-                    const T v0 = pop_enc<T>(fc[a].lo(), a, P, r), v1 = pop_enc<T>(fc[a].hi(), a, P, r >> 16);
+                    const unsigned r = store_bits<T, SR>(key, a, P);
+                    const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
@@ -872,8 +873,15 @@ __device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
 }
 
 // Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
-template <typename T, int EOS, int BC, int TX, int S, int G>
-__global__ void __launch_bounds__(G * TX / 2, resident_ctas(step_smem_bytes<T, TX, S, G>(), G * TX / 2))
+// the stochastic-rounding kernels hold the hash state too: they are compiled for at most
+// 8 resident CTAs (96 or more registers per thread) rather than spill
+__host__ __device__ constexpr int sr_blocks(int blocks, bool sr) {
+    return sr && blocks > 8 ? 8 : blocks;
+}
+
+template <typename T, int EOS, int BC, int TX, int S, int G, bool SR = false>
+__global__ void __launch_bounds__(G * TX / 2,
+                                  sr_blocks(resident_ctas(step_smem_bytes<T, TX, S, G>(), G * TX / 2), SR))
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
                const unsigned plane, const int rows, const int order, int *__restrict__ err) {
@@ -894,7 +902,7 @@ k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
     const int x0 = bx * TX;
     const int yb = by * rows;
     bool bad = false;
-    const int st = march<T, EOS, BC, TX, S, G>(&tin, gout, P, nx, ny, pitch, plane, x0,
+    const int st = march<T, EOS, BC, TX, S, G, SR>(&tin, gout, P, nx, ny, pitch, plane, x0,
                                                min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
@@ -940,8 +948,8 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
 }
 
 // Single lattice with the stage ring (same grid, parameters and results as k_pull_collide).
-template <typename T, int EOS, int BC, int TX, int S>
-__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>())
+template <typename T, int EOS, int BC, int TX, int S, bool SR = false>
+__global__ void __launch_bounds__(TX / 2, sr_blocks(stage_min_blocks<T, TX, S>(), SR))
 k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                      const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
                      const unsigned plane, const int rows, const int order, int *__restrict__ err) {
@@ -957,7 +965,7 @@ k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ go
     const int x0 = bx * TX;
     const int yb = by * rows;
     bool bad = false;
-    const int st = march_stage<T, EOS, BC, TX, S>(&tin, gout, P, nx, ny, pitch, plane, x0,
+    const int st = march_stage<T, EOS, BC, TX, S, SR>(&tin, gout, P, nx, ny, pitch, plane, x0,
                                                   min(TX, nx - x0), yb, min(yb + rows, ny) - yb,
                                                   ((by & 1) ^ order) ? -1 : 1, smem_raw, bad);
     if (threadIdx.x == 0 && st) atomicOr(err, st);
@@ -1003,10 +1011,12 @@ k_batch_step_stage(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *
 
 
 // K: ring kind, 0 = whole stored rows (k_pull_collide), 1 = stages (k_pull_collide_stage)
-template <typename T, int EOS, int BC, int TX, int S, int K>
+// SR: LB_BF16 with stochastic rounding (compiled apart, so the nearest-rounding kernels
+// carry none of its code)
+template <typename T, int EOS, int BC, int TX, int S, int K, bool SR = false>
 constexpr auto step_kernel() {
-    if constexpr (K == 0) return k_pull_collide<T, EOS, BC, TX, S, 1>;
-    else return k_pull_collide_stage<T, EOS, BC, TX, S>;
+    if constexpr (K == 0) return k_pull_collide<T, EOS, BC, TX, S, 1, SR>;
+    else return k_pull_collide_stage<T, EOS, BC, TX, S, SR>;
 }
 template <typename T, int TX, int S, int K>
 constexpr size_t step_kernel_smem() {
@@ -1018,10 +1028,17 @@ template <typename T, int EOS, int BC, int TX, int S, int K>
 cudaError_t step_variant(const Consts &c, const Geom &g, int rows, int order,
                          const CUtensorMap &tin, void *out, int *err, cudaStream_t st,
                          bool configure) {
-    auto kern = step_kernel<T, EOS, BC, TX, S, K>();
+    constexpr bool BF = std::is_same<T, __nv_bfloat16>::value;
+    auto kern = (BF && c.stochastic) ? step_kernel<T, EOS, BC, TX, S, K, BF>()
+                                     : step_kernel<T, EOS, BC, TX, S, K>();
     constexpr size_t smem = step_kernel_smem<T, TX, S, K>();
     if (configure) {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, EOS, BC, TX, S, K>(),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && BF)
+            e = cudaFuncSetAttribute(step_kernel<T, EOS, BC, TX, S, K, BF>(),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + rows - 1) / rows);
