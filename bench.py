@@ -397,10 +397,11 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, dist=N
     torch.cuda.synchronize()
     el_c = slowest(time.perf_counter() - t0)
     b.close()
-    rows_c = np.stack([res["theta"], res["converged"], res["failed"]], axis=1)
+    rows_c = np.stack([res["theta"], res["converged"], res["failed"], res["steps"]], axis=1)
     table = shard.gather_rows(rows_c, mine, n_lat, dist)
     n_conv = int(table[:, 1].sum())
-    lu_all = float(sum(d["side"] ** 2 * sweep.step_budget(d["side"]) for d in all_draws))
+    lu_all = float(sum(d["side"] ** 2 * table[k, 3] for k, d in enumerate(all_draws)))
+    n_ext = int(sum(table[k, 3] > sweep.step_budget(d["side"]) for k, d in enumerate(all_draws)))
     # one lattice per side alone through lb_step under the same protocol
     t_side = {}
     for s_ in sorted(set(sides.tolist())):
@@ -414,7 +415,9 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, dist=N
         sweep.converged_single(lat, int(budgets[i]), float(radii[i]))
         t_side[s_] = time.perf_counter() - t1
         lat.close()
-    t_seq_c = float(sum(t_side[int(s_)] for s_ in sides))
+    # a lattice's time alone scales with its step count (extensions included)
+    t_seq_c = float(sum(t_side[int(s_)] * res["steps"][i] / budgets[i]
+                        for i, s_ in enumerate(sides)))
     # FP64 batched reference of one lattice each of five sides spanning the range
     err = None
     if rank == 0:
@@ -441,7 +444,9 @@ def batched_sweep(lbm, torch, inputs, n_lat, steps, seed=1306, sample=24, dist=N
         "converged": {
             "protocol": "per-lattice budget 0.5 side^2 steps (>= 8192), retired when done; "
                         "sigma = mean of the last 2048 steps, converged if within 1 % of the "
-                        "same mean at 3/4 of the budget",
+                        "same mean at 3/4 of the budget, else run on by half the budget "
+                        "(at most twice) and compared with the previous reading",
+            "extended": n_ext,
             "seconds": round(el_c, 3), "lattice_updates": lu_all,
             "mlups": round(lu_all / el_c / 1e6, 1),
             "converged": n_conv, "converged_fraction": round(n_conv / n_lat, 4),

@@ -93,57 +93,73 @@ def step_budget(side: int, per_site2: float = 0.5, least: int = 8192) -> int:
 
 
 def converged_readings(b, budgets, radii, check_at: float = 0.75, window: int = WINDOW,
-                       tick: int = TICK):
+                       tick: int = TICK, extensions: int = 2, tol: float = 0.01):
     """Advance a batch whose lattices have budgets[i] steps each (multiples of `window`,
-    starting at step 0), retiring every lattice (lb_batch_set_active) once it has taken its
-    budget, so the work of a lattice is proportional to its own budget. The Laplace reading
-    of lattice i is averaged over the `window` steps before its budget (B) and over the
-    `window` steps before check_at x its budget (A, rounded to a window); the lattice counts
-    as converged when A and B differ by less than 1 %.
+    starting at step 0), retiring every lattice (lb_batch_set_active) once it is done, so
+    the work of a lattice is proportional to its own step count. The Laplace reading of
+    lattice i is averaged over the `window` steps before check_at x its budget (rounded to
+    a window) and over the `window` steps before its budget; the lattice is converged when
+    the two agree within `tol`. If they do not, it runs on for half its budget more (up to
+    `extensions` times) and its last two readings are compared again.
 
-    Returns a dict of arrays: theta (B), theta_check (A), rho_l, rho_v (B), failed,
-    converged."""
+    Returns a dict of arrays: theta (the last reading), theta_check (the one before),
+    rho_l, rho_v (last reading), failed, converged, steps (each lattice's total)."""
     budgets = np.asarray(budgets, dtype=np.int64)
     radii = np.asarray(radii, dtype=np.float64)
     n = len(budgets)
-    if np.any(budgets % window) or np.any(budgets < 2 * window):
-        raise ValueError("budgets must be multiples of the window, at least two windows")
-    checks = np.maximum(np.round(check_at * budgets / window).astype(np.int64) * window, window)
-    checks = np.minimum(checks, budgets - window)
-    win = [(checks - window, checks), (budgets - window, budgets)]
-    acc = np.zeros((n, 2, 3))
-    cnt = np.zeros((n, 2))
+    if np.any(budgets % window) or np.any(budgets < 4 * window):
+        raise ValueError("budgets must be multiples of the window, at least four windows")
+    checks = np.round(check_at * budgets / window).astype(np.int64) * window
+    checks = np.clip(checks, window, budgets - window)
+    ext = np.maximum((budgets // 2) // window * window, window)
+    end = checks.copy()                    # end of each lattice's next reading window
+    last_end = budgets.copy()              # step at which the lattice is checked next
+    acc = np.zeros((n, 3))
+    cnt = np.zeros(n)
+    prev = np.full((n, 3), np.nan)         # the reading before the current one
+    cur = np.full((n, 3), np.nan)
+    left = np.full(n, extensions)
     failed = np.zeros(n, dtype=bool)
+    conv = np.zeros(n, dtype=bool)
     active = np.ones(n, dtype=bool)
+    steps = np.zeros(n, dtype=np.int64)
     s = 0
     while active.any():
         nxt = s + tick
-        inw = [active & (nxt > lo) & (nxt <= hi) for lo, hi in win]
-        if inw[0].any() or inw[1].any():
+        inw = active & (nxt > end - window) & (nxt <= end)
+        if inw.any():
             b.step(tick)
+            steps[active] += tick
             s = nxt
             m = b.measure(radii)
-            for w in range(2):
-                acc[inw[w], w] += m[inw[w], :3]
-                cnt[inw[w], w] += 1
-            failed |= (inw[0] | inw[1]) & (m[:, 7] != 0)
+            acc[inw] += m[inw, :3]
+            cnt[inw] += 1
+            failed |= inw & (m[:, 7] != 0)
+            fin = inw & (end == s)         # a reading window closes
+            for i in np.flatnonzero(fin):
+                prev[i], cur[i] = cur[i], acc[i] / cnt[i]
+                acc[i], cnt[i] = 0.0, 0
+                if s < last_end[i]:        # the check reading: the next one ends the budget
+                    end[i] = last_end[i]
+                    continue
+                conv[i] = (not failed[i]) and abs(cur[i, 0] / prev[i, 0] - 1.0) < tol
+                if conv[i] or failed[i] or left[i] == 0:
+                    active[i] = False
+                else:                      # run on and read again
+                    left[i] -= 1
+                    last_end[i] += ext[i]
+                    end[i] = last_end[i]
+            if (fin & ~active).any():      # some lattice finished in this tick
+                b.set_active(active)
         else:
-            # jump to the next window start or budget of an active lattice
-            marks = np.concatenate([win[0][0][active], win[1][0][active], budgets[active]])
-            s_to = int(marks[marks > s].min())
+            # jump to the start of the next reading window of an active lattice
+            starts = (end - window)[active]
+            s_to = int(starts[starts > s].min()) if np.any(starts > s) else int(end[active].min())
             b.step(s_to - s)
+            steps[active] += s_to - s
             s = s_to
-        done = active & (budgets <= s)
-        if done.any():
-            active &= ~done
-            b.set_active(active)
-    theta = acc[:, 1, 0] / np.maximum(cnt[:, 1], 1)
-    theta_a = acc[:, 0, 0] / np.maximum(cnt[:, 0], 1)
-    conv = (~failed) & (np.abs(theta / theta_a - 1.0) < 0.01)
-    return {"theta": theta, "theta_check": theta_a,
-            "rho_l": acc[:, 1, 1] / np.maximum(cnt[:, 1], 1),
-            "rho_v": acc[:, 1, 2] / np.maximum(cnt[:, 1], 1),
-            "failed": failed, "converged": conv}
+    return {"theta": cur[:, 0], "theta_check": prev[:, 0], "rho_l": cur[:, 1],
+            "rho_v": cur[:, 2], "failed": failed, "converged": conv, "steps": steps}
 
 
 def converged_single(lat, budget: int, radius: float, check_at: float = 0.75,

@@ -102,12 +102,16 @@ def test_failed_runs_stay_failed_and_are_reported(monkeypatch):
 # ---- the converged sweep protocol (sweep.converged_readings) against a fake batch ------
 
 class FakeBatch:
-    """Stands in for lbm.Batch: lattice i reads theta_i(t) = target_i (1 + a_i cos(t / 50)
-    exp(-t / tau_i)); set_active must come at even step counts, like the library's."""
+    """Stands in for lbm.Batch: lattice i reads theta_i(t) = target_i (1 + a_i cos(t / p_i)
+    exp(-t / tau_i) + d_i exp(-t / tau_d)); set_active must come at even step counts, like
+    the library's."""
 
-    def __init__(self, target, amp, tau):
+    def __init__(self, target, amp, tau, period=None, drift=None, tau_d=3000.0):
         self.target, self.amp, self.tau = map(np.asarray, (target, amp, tau))
         self.n = len(self.target)
+        self.period = np.full(self.n, 50.0) if period is None else np.asarray(period)
+        self.drift = np.zeros(self.n) if drift is None else np.asarray(drift)
+        self.tau_d = tau_d
         self.t = np.zeros(self.n)
         self.active = np.ones(self.n, dtype=bool)
         self.steps = 0
@@ -119,7 +123,8 @@ class FakeBatch:
         self.steps += k
 
     def measure(self, radii):
-        th = self.target * (1 + self.amp * np.cos(self.t / 50.0) * np.exp(-self.t / self.tau))
+        th = self.target * (1 + self.amp * np.cos(self.t / self.period) * np.exp(-self.t / self.tau)
+                            + self.drift * np.exp(-self.t / self.tau_d))
         out = np.zeros((self.n, 8))
         out[:, 0], out[:, 1], out[:, 2] = th, 0.3, 0.02
         return out
@@ -140,9 +145,10 @@ def test_converged_readings_retires_each_lattice_at_its_budget():
     budgets = np.array([8192, 16384, 8192, 32768])
     b = FakeBatch(target=[1e-3, 2e-3, 3e-3, 4e-3], amp=[0.5, 0.5, 0.5, 0.5],
                   tau=[500.0, 500.0, 1e9, 500.0])
-    r = sweep.converged_readings(b, budgets, np.ones(4))
+    r = sweep.converged_readings(b, budgets, np.ones(4), extensions=0)
     # every lattice took exactly its budget and the batch stopped with the last one
     assert np.array_equal(b.t, budgets) and b.steps == budgets.max()
+    assert np.array_equal(r["steps"], budgets)
     # retirements at the budgets, in order
     assert [c[0] for c in b.calls] == [8192, 16384, 32768]
     # damped lattices read their target; the undamped one (tau = inf) oscillates between
@@ -154,9 +160,33 @@ def test_converged_readings_retires_each_lattice_at_its_budget():
     ts = np.arange(8192 - 2048 + 64, 8192 + 1, 64)
     want = np.mean(3e-3 * (1 + 0.5 * np.cos(ts / 50.0) * np.exp(-ts / 1e9)))
     assert r["theta"][2] == pytest.approx(want, rel=1e-12)
+    # the check reading: the window before 3/4 of the budget
+    tc = np.arange(6144 - 2048 + 64, 6144 + 1, 64)
+    assert r["theta_check"][2] == pytest.approx(
+        np.mean(3e-3 * (1 + 0.5 * np.cos(tc / 50.0) * np.exp(-tc / 1e9))), rel=1e-12)
+
+
+def test_converged_readings_runs_slow_lattices_on():
+    # lattice 1 still drifts at its budget (exp(-t/3000)): it runs on for half its budget at
+    # a time until two readings agree (3 % apart at 6144/8192 steps, 2.4 % at 8192/12288,
+    # 0.6 % at 12288/16384); lattice 0 converges at once; lattice 2 swings slowly (a period
+    # of 12 600 steps, undamped) and stops unconverged after the allowed extensions
+    budgets = np.array([8192, 8192, 8192])
+    b = FakeBatch(target=[1e-3, 1e-3, 1e-3], amp=[0.5, 0.0, 0.3], tau=[300.0, 1.0, 1e12],
+                  period=[50.0, 50.0, 2000.0], drift=[0.0, 0.5, 0.0])
+    r = sweep.converged_readings(b, budgets, np.ones(3), extensions=2)
+    assert r["steps"][0] == 8192 and r["converged"][0]
+    assert r["steps"][1] == 16384 and r["converged"][1]
+    assert r["steps"][2] == 8192 + 2 * 4096 and not r["converged"][2]
+    assert np.array_equal(b.t, r["steps"])
+    assert r["theta"][1] == pytest.approx(1e-3, rel=0.005)   # the drift left: 0.3 %
+    # the batch was told each time a lattice stopped, at the step it stopped
+    assert [c[0] for c in b.calls] == [8192, 16384]
 
 
 def test_converged_readings_rejects_budgets_off_the_window():
     b = FakeBatch([1.0], [0.0], [1.0])
     with pytest.raises(ValueError):
         sweep.converged_readings(b, [5000], [1.0])
+    with pytest.raises(ValueError):
+        sweep.converged_readings(b, [4096], [1.0])   # fewer than four windows
