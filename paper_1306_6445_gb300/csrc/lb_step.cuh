@@ -974,8 +974,10 @@ k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ go
 }
 
 // Many lattices with the stage ring (as k_batch_step).
+// the item loop keeps the lattice's constants in registers too: compiled for at most 10
+// resident CTAs (100 registers) rather than re-read them from the table or spill
 template <typename T, int EOS, int TX, int S>
-__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>())
+__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>() > 10 ? 10 : stage_min_blocks<T, TX, S>())
 k_batch_step_stage(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
                    const BatchItem *__restrict__ items, const int n_items, const int phase,
                    int *__restrict__ errs) {
