@@ -1,7 +1,8 @@
-// Templates of the step kernel shared by the per-precision translation units
-// (lb_step_f32.cu, lb_step_f64.cu, lb_step_bf16.cu, lb_batch_kernels.cu) and the
-// auxiliary kernels (lb_kernels.cu). Everything here has internal linkage; each unit
-// instantiates what it launches.
+// Templates of the step kernels shared by the translation units that instantiate them
+// (lb_step_<type>.cu: the whole-row ring, lb_step_<type>_stage.cu: the stage ring, one
+// pair per storage type; lb_batch_kernels.cu, lb_batch_stage.cu: the batched step) and by
+// the auxiliary kernels (lb_kernels.cu). Everything here has internal linkage; each unit
+// instantiates what it launches (LB_STEP_UNIT / LB_BATCH_UNIT at the end of this file).
 //
 // Kernels of the D2Q9 MRT pseudopotential update with the surface-tension source term
 // (Li & Luo, arXiv 1306.6445, Sec. II and IV) for sm_103a.
@@ -14,20 +15,23 @@
 // at the site itself: that f* is the g of the next step (Eq. 4 is the pull). So every step
 // reads each population once and writes it once, with aligned, site-local stores.
 //
-// Each population plane has ny rows of `pitch` elements. Column x of the lattice lives at
-// element x + GH<T> of its row (8 for float storage, 4 otherwise); elements GH-2, GH-1 and
-// nx+GH, nx+GH+1 are ghost copies of columns nx-2, nx-1 and 0, 1 (periodic images),
-// rewritten by every kernel that writes g.
+// Population a lives in plane plane_of(a) (groups of three by the row it is pulled from,
+// see lb_internal.h). Each plane has ny rows of `pitch` elements. Column x of the lattice
+// lives at element x + GH<T> of its row (8 for float storage, 4 otherwise); elements GH-2,
+// GH-1 and nx+GH, nx+GH+1 are ghost copies of columns nx-2, nx-1 and 0, 1 (periodic
+// images), rewritten by every kernel that writes g.
 //
-// Hot kernel (k_pull_collide): a CTA owns a strip of TX columns (two per thread) and
-// marches up `rows` rows. Rows of g (9 planes x (TX + AL + 4) columns, i.e. the strip plus an
-// apron of AL columns on the left, 8 for float storage and 4 otherwise, and 4 on the right)
-// arrive through a ring of S shared-memory stages fed by
-// 3-D TMA loads (cp.async.bulk.tensor) completing on per-stage mbarriers. From the ring a
-// thread pulls f for its two sites, forms rho and psi (psi is never stored in HBM; a
-// four-row psi ring with one halo column on each side lives in shared memory), then
+// Hot kernels: a CTA owns a strip of TX columns (two per thread) and marches over `rows`
+// rows. The populations arrive in shared memory through 3-D TMA loads
+// (cp.async.bulk.tensor) completing on per-stage mbarriers: k_pull_collide_stage (the
+// default) stages, per psi row, exactly the three plane groups that row is pulled from,
+// one stage in use at a time; k_pull_collide stages whole rows of the strip (9 planes x
+// (TX + AL + 4) columns: the strip, an apron of AL columns on the left, 8 for float
+// storage and 4 otherwise, and 4 on the right), three rows in use at a time. From the
+// stage a thread pulls f for its two sites, forms rho and psi (psi is never stored in
+// HBM; a four-row psi ring with one halo column on each side lives in shared memory), then
 // collides (Eqs. 3-8, 17-19) in packed two-lane arithmetic and stores f* as one 8-byte
-// (FP32) or 16-byte (FP64) store per population.
+// (FP32) or 16-byte (FP64) store per population. Both give identical results.
 
 
 
@@ -873,15 +877,16 @@ __device__ __forceinline__ void init_ring_barriers(uint64_t *bar, bool reuse) {
 }
 
 // Single lattice: CTA (bx, by) owns strip bx and row block by of one lattice.
-// the stochastic-rounding kernels hold the hash state too: they are compiled for at most
-// 8 resident CTAs (96 or more registers per thread) rather than spill
-__host__ __device__ constexpr int sr_blocks(int blocks, bool sr) {
-    return sr && blocks > 8 ? 8 : blocks;
+// the stochastic-rounding kernels hold the hash state too: they are compiled for as many
+// resident CTAs as 128 registers per thread allow (8 at 64 threads) rather than spill
+__host__ __device__ constexpr int sr_blocks(int blocks, int threads, bool sr) {
+    return !sr || blocks * threads * 128 <= 65536 ? blocks
+                                                  : (65536 / (threads * 128) > 0 ? 65536 / (threads * 128) : 1);
 }
 
 template <typename T, int EOS, int BC, int TX, int S, int G, bool SR = false>
 __global__ void __launch_bounds__(G * TX / 2,
-                                  sr_blocks(resident_ctas(step_smem_bytes<T, TX, S, G>(), G * TX / 2), SR))
+                                  sr_blocks(resident_ctas(step_smem_bytes<T, TX, S, G>(), G * TX / 2), G * TX / 2, SR))
 k_pull_collide(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
                const unsigned plane, const int rows, const int order, int *__restrict__ err) {
@@ -949,7 +954,7 @@ k_batch_step(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__rest
 
 // Single lattice with the stage ring (same grid, parameters and results as k_pull_collide).
 template <typename T, int EOS, int BC, int TX, int S, bool SR = false>
-__global__ void __launch_bounds__(TX / 2, sr_blocks(stage_min_blocks<T, TX, S>(), SR))
+__global__ void __launch_bounds__(TX / 2, sr_blocks(stage_min_blocks<T, TX, S>(), TX / 2, SR))
 k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ gout,
                      const DevConsts<Arith<T>> P, const int nx, const int ny, const int pitch,
                      const unsigned plane, const int rows, const int order, int *__restrict__ err) {
@@ -974,10 +979,18 @@ k_pull_collide_stage(const __grid_constant__ CUtensorMap tin, T *__restrict__ go
 }
 
 // Many lattices with the stage ring (as k_batch_step).
-// the item loop keeps the lattice's constants in registers too: compiled for at most 10
-// resident CTAs (100 registers) rather than re-read them from the table or spill
+// The item loop keeps the lattice's constants in registers on top of the single kernel's
+// state: FP32 and BF16 storage are compiled for at most 10 resident CTAs (96 registers at
+// 64 threads), FP64 for as many as 224 registers per thread allow, rather than re-read the
+// constants from the table or spill.
+template <typename T, int TX, int S>
+__host__ __device__ constexpr int batch_stage_blocks() {
+    constexpr int smb = stage_min_blocks<T, TX, S>();
+    constexpr int cap = sizeof(T) == 8 ? 65536 / (TX / 2 * 224) : 10;
+    return smb < cap ? smb : (cap > 0 ? cap : 1);
+}
 template <typename T, int EOS, int TX, int S>
-__global__ void __launch_bounds__(TX / 2, stage_min_blocks<T, TX, S>() > 10 ? 10 : stage_min_blocks<T, TX, S>())
+__global__ void __launch_bounds__(TX / 2, batch_stage_blocks<T, TX, S>())
 k_batch_step_stage(const CUtensorMap *__restrict__ maps, const BatchLattice<T> *__restrict__ lats,
                    const BatchItem *__restrict__ items, const int n_items, const int phase,
                    int *__restrict__ errs) {

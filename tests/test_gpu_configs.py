@@ -13,12 +13,15 @@
   Maxwell densities, and their scale is the flat-interface tension between those.
 - The same 2048 x 2048 droplet converged (200 000 steps, kappa = 0.6): the Laplace reading
   within 5 % of the flat-interface surface tension, FP32 and FP64 within 0.5 %.
-- 4096 x 2048 capillary wave with walls in y (layer height 1024, wavelength 4096/k,
-  amplitude 0.01 wavelength), FP32, 50000 steps. At this scale the period (about 1.1e5
-  steps at k = 4, and longer at k = 1, 2) exceeds the run, so the frequency is fitted to
-  the interface height over the part of a period the run covers, and compared with the
-  finite-depth dispersion relation (Eq. 24 read with omega^2) using the flat-interface
-  surface tension of Eq. 22."""
+- 4096 x 2048 capillary wave with walls in y (layer height 1024, wavelength 4096/k for
+  k = 1, 2, 4, amplitude 0.01 wavelength), FP32, kappa = 0 and 0.5. At this size the
+  period is 1.1e5 steps at k = 4 and 3e5 and 9e5 at k = 2 and 1, so 50000 steps show less
+  than half a period: each wave runs instead to its second zero crossing (k = 4, 2; half a
+  period between the two, clear of the start from rest) or its first (k = 1; a quarter
+  period). The amplitude of the seeded Fourier mode of the interface height gives the
+  crossings; the frequency is compared with the finite-depth dispersion relation (Eq. 24
+  read with omega^2) at the flat-interface surface tension of Eq. 22, and the ratio of the
+  two kappas with sqrt(1/2), the ratio of their surface tensions' square roots."""
 import numpy as np
 import pytest
 
@@ -31,7 +34,6 @@ from _util import oracle_params
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-scipy_optimize = pytest.importorskip("scipy.optimize")
 
 
 @pytest.fixture(scope="module")
@@ -133,42 +135,72 @@ def test_2048_droplet_converged_surface_tension_fp32_and_fp64(lbm):
     assert ra32 == pytest.approx(ra64, rel=5e-3)
 
 
-@pytest.mark.parametrize("kappa", [0.0, 0.5])
-def test_4096x2048_capillary_wave_frequency_follows_the_dispersion_relation(lbm, kappa):
-    nx, ny, h, k = 4096, 2048, 1024.0, 4
+def _zero_crossings(ts, ys, half=2000.0):
+    """Times where ys changes sign, each from a least-squares line through the samples
+    within `half` steps of the sign change (the mode amplitude carries small acoustic
+    ripples); sign changes closer than 2 half to the previous one count once."""
+    out = []
+    for i in range(len(ys) - 1):
+        if ys[i] * ys[i + 1] < 0:
+            tc = 0.5 * (ts[i] + ts[i + 1])
+            if out and tc - out[-1] < 2.0 * half:
+                continue
+            s = np.abs(ts - tc) <= half
+            b, a = np.polyfit(ts[s] - tc, ys[s], 1)
+            out.append(tc - a / b)
+    return out
+
+
+# steps to the first two zero crossings of the mode (the second only where it is timed)
+_CAP_STEPS = {(4, 0.0): 90000, (4, 0.5): 130000, (2, 0.0): 260000, (2, 0.5): 365000,
+              (1, 0.0): 265000, (1, 0.5): 370000}
+
+
+@pytest.mark.parametrize("k", [4, 2, 1])
+def test_4096x2048_capillary_wave_frequency_follows_the_dispersion_relation(lbm, k):
+    nx, ny, h = 4096, 2048, 1024.0
     lam = nx / k
     nu = 0.1     # the CS vapour (rho_v = 0.008) leaves the EOS branch at nu = 0.02
     eos = lbm.cs_eos(0.8)
     oeos = OE.EOS(kind="cs", T=eos.T)
     pv, pl, _ = OE.mechanical_stability(oeos, -1.0, 0.0)
-    theta = OE.flat_surface_tension(oeos, -1.0, kappa)
-    kk = 2 * np.pi / lam
-    omega0 = np.sqrt(theta * kk ** 3 / (pl / np.tanh(kk * h) + pv / np.tanh(kk * (ny - h))))
-    lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=kappa, rates=lbm.RateParams.from_viscosity(nu),
-                      prec="fp32", walls_y=True)
-    lat.set_rho_u(I.layer_density(nx, ny, h, pl, pv, width=2.0, amplitude=0.01 * lam,
-                                  wavenumber=k))
-    lat.autotune(2)
-    ts, hs = [], []
     mid = 0.5 * (pl + pv)
-    while lat.steps_done <= 50000:
-        # a crest column, from the GPU's interface heights (equal to the oracle's reading of
-        # the same density field, see test_gpu_diagnostics)
-        hs.append(lat.interface_height(mid)[0] - h)
-        ts.append(lat.steps_done)
-        lat.step(1000)
-    lat.close()
-    ts, hs = np.array(ts, float), np.array(hs)
-
-    # the crest height oscillates about the undisturbed level (mass conservation keeps the
-    # mean layer height): a damped cosine without an offset
-    def model(t, a, w, g):
-        return a * np.exp(-g * t) * np.cos(w * t)
-
-    p, _ = scipy_optimize.curve_fit(model, ts, hs, p0=(hs[0], omega0, 1e-6), maxfev=20000)
-    a, w, g = p
-    print("crest height every 5000 steps:", np.round(hs[::5], 3))
-    print(f"kappa {kappa}: omega fitted {w:.5g}, dispersion {omega0:.5g} "
-          f"({w / omega0 - 1:+.2%}), amplitude {a:.3g} (set {0.01 * lam:.3g}), damping {g:.3g}")
-    assert abs(hs[0] - 0.01 * lam) < 1.0
-    assert w == pytest.approx(omega0, rel=0.05)
+    x = np.arange(nx)
+    basis = 2.0 / nx * np.cos(2.0 * np.pi * k * x / nx)
+    omega, omega0 = {}, {}
+    for kappa in (0.0, 0.5):
+        theta = OE.flat_surface_tension(oeos, -1.0, kappa)
+        omega0[kappa] = 2.0 * np.pi / D.capillary_period(theta, lam, pl, pv, h, ny - h)
+        lat = lbm.Lattice(nx, ny, eos, -1.0, kappa=kappa, rates=lbm.RateParams.from_viscosity(nu),
+                          prec="fp32", walls_y=True)
+        lat.set_rho_u(I.layer_density(nx, ny, h, pl, pv, width=2.0, amplitude=0.01 * lam,
+                                      wavenumber=k))
+        lat.autotune(2)
+        ts, amp = [], []
+        while lat.steps_done <= _CAP_STEPS[(k, kappa)]:
+            # amplitude of the seeded mode, projected from the GPU's interface heights
+            # (equal to the oracle's reading of the same density field, test_gpu_diagnostics)
+            amp.append(float((lat.interface_height(mid) - h) @ basis))
+            ts.append(lat.steps_done)
+            lat.step(500)
+        lat.close()
+        ts, amp = np.array(ts, float), np.array(amp)
+        z = _zero_crossings(ts, amp)
+        assert abs(amp[0] - 0.01 * lam) < 1.0
+        print(f"k {k}, kappa {kappa}: mode amplitude every 10000 steps {np.round(amp[::20], 2)}")
+        if k == 1:
+            # a quarter period: from rest to the first zero crossing
+            assert len(z) >= 1
+            omega[kappa] = 0.5 * np.pi / z[0]
+        else:
+            # half a period, between the first two zero crossings (clear of the start)
+            assert len(z) >= 2
+            omega[kappa] = np.pi / (z[1] - z[0])
+        print(f"  crossings {np.round(z, 0)}: omega {omega[kappa]:.5g}, finite-depth relation "
+              f"{omega0[kappa]:.5g} ({omega[kappa] / omega0[kappa] - 1:+.2%}), viscous shift "
+              f"estimate {-0.5 * (2 * nu * (2 * np.pi / lam) ** 2 / omega0[kappa]) ** 2:+.2%}")
+        assert omega[kappa] == pytest.approx(omega0[kappa], rel=0.04 if k > 1 else 0.06)
+    # kappa = 0.5 halves the surface tension: the frequency drops by sqrt(2)
+    ratio = omega[0.5] / omega[0.0]
+    print(f"  omega(kappa 0.5) / omega(kappa 0) = {ratio:.4f} (sqrt(0.5) = {np.sqrt(0.5):.4f})")
+    assert ratio == pytest.approx(np.sqrt(0.5), rel=0.02)
