@@ -88,9 +88,25 @@ inline DevConsts<T> to_dev(const Consts &c) {
 // at different inline sites: a site's psi is bitwise the same wherever it is computed. --
 __device__ __forceinline__ float lb_exp(float v) { return __expf(v); }
 __device__ __forceinline__ double lb_exp(double v) { return exp(v); }
-__device__ __forceinline__ float lb_div(float a, float b) { return __fdividef(a, b); }
+// FP32 reciprocal and reciprocal square root: one hardware approximation each (PTX
+// rcp.approx / rsqrt.approx, within two ulp), subnormal inputs and results flushed to zero
+// (.ftz): the update meets no subnormal density, pressure or potential, and the
+// non-flushing forms add range fix-ups around every approximation.
+__device__ __forceinline__ float rcp_ftz(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float lb_div(float a, float b) { return __fmul_rn(a, rcp_ftz(b)); }
 __device__ __forceinline__ double lb_div(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ float lb_sqrt_pos(float v) { return __fmul_rn(v, rsqrtf(v)); }   // v > 0
+__device__ __forceinline__ float lb_rcp(float v) { return rcp_ftz(v); }
+__device__ __forceinline__ double lb_rcp(double v) { return __ddiv_rn(1.0, v); }
+__device__ __forceinline__ float lb_sqrt_pos(float v) { return __fmul_rn(v, rsqrt_ftz(v)); }   // v > 0
 __device__ __forceinline__ double lb_sqrt_pos(double v) { return __dsqrt_rn(v); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
@@ -313,7 +329,7 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V m8 = s57 - s68;
 
     // Eq. 6 velocity and Eq. 3 equilibria
-    const V rinv(lb_div(T(1), rho.lo()), lb_div(T(1), rho.hi()));
+    const V rinv(lb_rcp(rho.lo()), lb_rcp(rho.hi()));
     const V vx = vfma(half, Fx, jx) * rinv;
     const V vy = vfma(half, Fy, jy) * rinv;
     const V vxx = vx * vx, vyy = vy * vy;
