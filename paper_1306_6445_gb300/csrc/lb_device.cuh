@@ -218,7 +218,14 @@ struct V2<float> {
 __device__ __forceinline__ V2<float> operator+(V2<float> a, V2<float> b) { return __fadd2_rn(a.v, b.v); }
 __device__ __forceinline__ V2<float> operator*(V2<float> a, V2<float> b) { return __fmul2_rn(a.v, b.v); }
 __device__ __forceinline__ V2<float> operator-(V2<float> a, V2<float> b) {
-    return __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v);   // exactly a - b
+    // the packed subtraction (PTX sub.rn.f32x2), lane by lane the rounded a - b
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+    return r;
 }
 __device__ __forceinline__ V2<float> vfma(V2<float> a, V2<float> b, V2<float> c) {
     return __ffma2_rn(a.v, b.v, c.v);
