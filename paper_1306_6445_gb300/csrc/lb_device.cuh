@@ -5,9 +5,10 @@
 // transformation matrix M (Sec. II). All constants below are written out by hand.
 //
 // The collision works on PAIRS of sites held in a two-lane vector: in FP32 the lanes are
-// packed into one register pair and every add / multiply / fma is a single packed
-// instruction of sm_100-class GPUs (__fadd2_rn, __fmul2_rn, __ffma2_rn, each lane rounded
-// exactly like the scalar operation); in FP64 the two lanes are plain scalar doubles.
+// packed into one register pair and every add / subtract / multiply / fma is a single
+// packed instruction of sm_100-class GPUs (__fadd2_rn, sub.rn.f32x2, __fmul2_rn,
+// __ffma2_rn, each lane rounded exactly like the scalar operation); in FP64 the two lanes
+// are plain scalar doubles.
 #pragma once
 
 #include <cuda_bf16.h>
