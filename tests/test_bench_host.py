@@ -1,6 +1,6 @@
 """Host-side helpers of bench.py (CPU): the clock summary taken from nvidia-smi lines, the
 lookup of figures in a committed ncu summary (used only while its kernel-source hash is
-current) and the workload description both arms print."""
+current), the workload description both arms print and the splash grid's reruns."""
 import importlib.util
 import os
 import sys
@@ -60,3 +60,26 @@ def test_both_arms_describe_the_same_workload(bench):
     c = bench.bench_config(2048, 2048, 100, 4)
     assert c["workload"] == bench.WORKLOAD and c["parallelism"] == "replicas4"
     assert c["nx"] == c["ny"] == 2048 and c["lb_steps_per_step"] == 100
+
+
+def test_splash_points_that_break_early_run_again_warmer(bench, monkeypatch):
+    """The splash grid reruns, at the warmer temperature, exactly the points that left the
+    EOS branch before t* = 1.75 (4000 steps at D = 400, U = 0.05 from t* = 0.05 is
+    t* = 0.55; 28000 steps is t* = 3.55), and lists both runs of such a point."""
+    calls = []
+
+    def fake_point(lbm, torch, net, nx, ny, D, We, Re, U, t_over_tc, steps):
+        calls.append((We, Re, t_over_tc))
+        early = We == 800.0 and t_over_tc == 0.65
+        late = We == 200.0 and Re == 1000.0
+        done = 4000 if early else (28000 if late else steps)
+        return {"We": We, "Re": Re, "t_over_tc": t_over_tc, "steps_done": done,
+                "breakdown": "LB_EDOMAIN" if (early or late) else None}
+
+    monkeypatch.setattr(bench, "splash_point", fake_point)
+    out = bench.splash_leg(None, None, None, steps=40000)
+    assert calls == [(200.0, 500.0, 0.65), (200.0, 1000.0, 0.65),
+                     (800.0, 500.0, 0.65), (800.0, 500.0, 0.70),
+                     (800.0, 1000.0, 0.65), (800.0, 1000.0, 0.70)]
+    assert [(p["We"], p["Re"], p["t_over_tc"]) for p in out["points"]] == calls
+    assert "0.7Tc" in out["workload"]
