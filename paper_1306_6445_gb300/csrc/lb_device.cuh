@@ -106,7 +106,7 @@ __device__ __forceinline__ float rsqrt_ftz(float v) {
 __device__ __forceinline__ float lb_div(float a, float b) { return __fmul_rn(a, rcp_ftz(b)); }
 __device__ __forceinline__ double lb_div(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float lb_rcp(float v) { return rcp_ftz(v); }
-__device__ __forceinline__ double lb_rcp(double v) { return __ddiv_rn(1.0, v); }
+__device__ __forceinline__ double lb_rcp(double v) { return __drcp_rn(v); }   // = 1 / v rounded
 __device__ __forceinline__ float lb_sqrt_pos(float v) { return __fmul_rn(v, rsqrt_ftz(v)); }   // v > 0
 __device__ __forceinline__ double lb_sqrt_pos(double v) { return __dsqrt_rn(v); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
@@ -231,6 +231,7 @@ __device__ __forceinline__ V2<float> operator-(V2<float> a, V2<float> b) {
 __device__ __forceinline__ V2<float> vfma(V2<float> a, V2<float> b, V2<float> c) {
     return __ffma2_rn(a.v, b.v, c.v);
 }
+__device__ __forceinline__ V2<float> operator-(V2<float> a) { return V2<float>(-a.v.x, -a.v.y); }
 
 template <>
 struct V2<double> {
@@ -253,6 +254,7 @@ __device__ __forceinline__ V2<double> operator-(V2<double> a, V2<double> b) {
 __device__ __forceinline__ V2<double> vfma(V2<double> a, V2<double> b, V2<double> c) {
     return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
 }
+__device__ __forceinline__ V2<double> operator-(V2<double> a) { return {-a.x, -a.y}; }
 
 // psi of two densities; lane by lane the same operations, in the same order and with
 // the same rounding, as eos_psi (so a site's psi does not depend on which lane or which
@@ -313,11 +315,11 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V mGpc = V::all(-P.G) * pc;
     const V Fx = mGpc * Sx;
     const V Fy = mGpc * Sy;
-    const V dsum = ((pn[5] + pn[6]) + (pn[7] + pn[8])) - four * pc;
+    const V dsum = vfma(V::all(T(-4)), pc, (pn[5] + pn[6]) + (pn[7] + pn[8]));
     const V qpre = V::all(P.kG2) * pc;
     const V tdsum = twelfth * dsum;
-    const V Qxx = qpre * vfma(third, (pn[1] + pn[3]) - two * pc, tdsum);
-    const V Qyy = qpre * vfma(third, (pn[2] + pn[4]) - two * pc, tdsum);
+    const V Qxx = qpre * vfma(third, vfma(V::all(T(-2)), pc, pn[1] + pn[3]), tdsum);
+    const V Qyy = qpre * vfma(third, vfma(V::all(T(-2)), pc, pn[2] + pn[4]), tdsum);
     const V Qxy = qpre * (twelfth * ((pn[5] + pn[7]) - (pn[6] + pn[8])));
 
     // moments m = M f
@@ -329,8 +331,8 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V rho = f[0] + (axis + diag);
     const V jx = d13 + (d57 - d68);
     const V jy = d24 + (d57 + d68);
-    const V m1 = vfma(two, diag, vfma(V::all(T(-4)), f[0], V::all(T(0)) - axis));
-    const V m2 = vfma(four, f[0], diag - two * axis);
+    const V m1 = vfma(two, diag, vfma(V::all(T(-4)), f[0], -axis));
+    const V m2 = vfma(four, f[0], vfma(V::all(T(-2)), axis, diag));
     const V m4 = vfma(V::all(T(-2)), d13, d57 - d68);
     const V m6 = vfma(V::all(T(-2)), d24, d57 + d68);
     const V m7 = ax - ay;
@@ -361,11 +363,11 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V ms1 = vfma(V::all(P.e_keep), m1, vfma(V::all(P.s_e), meq1,
                   vfma(V::all(P.e_half), S1, V::all(P.e_src) * tr)));
     const V ms2 = vfma(V::all(P.z_keep), m2, vfma(V::all(P.s_z), meq2,
-                  V::all(T(0)) - vfma(V::all(P.z_half), S1, V::all(P.z_src) * tr)));
+                  -vfma(V::all(P.z_half), S1, V::all(P.z_src) * tr)));
     const V ms3 = jx + Fx;
-    const V ms4 = vfma(V::all(P.q_keep), m4, V::all(T(0)) - vfma(V::all(P.s_q), rvx, V::all(P.q_half) * Fx));
+    const V ms4 = vfma(V::all(P.q_keep), m4, -vfma(V::all(P.s_q), rvx, V::all(P.q_half) * Fx));
     const V ms5 = jy + Fy;
-    const V ms6 = vfma(V::all(P.q_keep), m6, V::all(T(0)) - vfma(V::all(P.s_q), rvy, V::all(P.q_half) * Fy));
+    const V ms6 = vfma(V::all(P.q_keep), m6, -vfma(V::all(P.s_q), rvy, V::all(P.q_half) * Fy));
     V vkeep = V::all(P.v_keep), vs = V::all(P.s_v), vhalf = V::all(P.v_half);
     V vsrc = V::all(P.v_src);
     if constexpr (VSW) {
