@@ -84,7 +84,8 @@ inline DevConsts<T> to_dev(const Consts &c) {
 }
 
 // ---- scalar helpers: FP32 uses the hardware approximations (a few ulp, far inside the
-// FP32 error budget), FP64 the IEEE-rounded operations. Every add / multiply / fma is an
+// FP32 error budget), FP64 IEEE-rounded operations (its division within one ulp: the
+// product with the rounded reciprocal). Every add / multiply / fma is an
 // explicit round-to-nearest intrinsic, so the compiler cannot contract them differently
 // at different inline sites: a site's psi is bitwise the same wherever it is computed. --
 __device__ __forceinline__ float lb_exp(float v) { return __expf(v); }
@@ -104,7 +105,8 @@ __device__ __forceinline__ float rsqrt_ftz(float v) {
     return r;
 }
 __device__ __forceinline__ float lb_div(float a, float b) { return __fmul_rn(a, rcp_ftz(b)); }
-__device__ __forceinline__ double lb_div(double a, double b) { return __ddiv_rn(a, b); }
+// FP64 a / b as a times the correctly rounded 1 / b (within one ulp of the quotient)
+__device__ __forceinline__ double lb_div(double a, double b) { return __dmul_rn(a, __drcp_rn(b)); }
 __device__ __forceinline__ float lb_rcp(float v) { return rcp_ftz(v); }
 __device__ __forceinline__ double lb_rcp(double v) { return __drcp_rn(v); }   // = 1 / v rounded
 __device__ __forceinline__ float lb_sqrt_pos(float v) { return __fmul_rn(v, rsqrt_ftz(v)); }   // v > 0
