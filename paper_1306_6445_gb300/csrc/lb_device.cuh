@@ -39,6 +39,7 @@ struct DevConsts {
     T e_keep, e_half, e_src, z_keep, z_half, z_src, q_keep, q_half, v_keep, v_half, v_src;
     // storage shift w_a rho_s: LB_BF16 stores f_a - w_a rho_s (zero for FP32 / FP64)
     T wshift[9];
+    T rho_s;
     // nu(rho) (open-boundary kernels only): sites with rho < rho_sw relax p_xx, p_xy at
     // s_vV; the Eq. 17 coefficients for that rate
     T rho_sw, s_vV, v_keep_V, v_half_V, v_src_V;
@@ -73,6 +74,7 @@ inline DevConsts<T> to_dev(const Consts &c) {
     d.v_keep = T(1.0 - c.s_v); d.v_half = T(1.0 - 0.5 * c.s_v); d.v_src = T(-c.s_v);
     for (int a = 0; a < 9; ++a)
         d.wshift[a] = T((a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0)) * c.shift_rho);
+    d.rho_s = T(c.shift_rho);
     d.rho_sw = T(c.rho_sw);
     d.s_vV = T(c.s_v_vapour);
     d.v_keep_V = T(1.0 - c.s_v_vapour);
@@ -301,7 +303,11 @@ __device__ __forceinline__ V2<T> eos_psi2(V2<T> rho, const DevConsts<T> &P, bool
 //   m*_k = (1 - s_k) m_k + s_k m_eq_k + (1 - s_k/2) S_k + C_k for the other moments.
 //   VSW: nu(rho) of Sec. V.C, the rate of p_xx, p_xy (and the weight of their source
 //   terms) taken per site as s_v where rho >= rho_sw, else s_vV.
-template <typename T, bool VSW = false>
+//   SH (LB_BF16): f holds the stored shifted populations f_a - w_a rho_s. The shift only
+//   moves the moments rho, e and zeta (M w = (1, -2, 1, 0, ..., 0)), so those are corrected
+//   by rho_s, and the same is taken off m* before M^-1 gives the shifted f* that is stored;
+//   f*_0 from mass conservation reads the same in shifted terms.
+template <typename T, bool VSW = false, bool SH = false>
 __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9],
                                              const DevConsts<T> &P) {
     using V = V2<T>;
@@ -330,11 +336,19 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V s57 = f[5] + f[7], s68 = f[6] + f[8];
     const V d57 = f[5] - f[7], d68 = f[6] - f[8];
     const V axis = ax + ay, diag = s57 + s68;
-    const V rho = f[0] + (axis + diag);
+    const V rsum = f[0] + (axis + diag);       // sum of f (of the shifted f when SH)
+    V rs;                                      // rho_s in both lanes (SH)
+    if constexpr (SH) rs = V::all(P.rho_s);
+    V rho = rsum;
+    if constexpr (SH) rho = rsum + rs;
     const V jx = d13 + (d57 - d68);
     const V jy = d24 + (d57 + d68);
-    const V m1 = vfma(two, diag, vfma(V::all(T(-4)), f[0], -axis));
-    const V m2 = vfma(four, f[0], vfma(V::all(T(-2)), axis, diag));
+    V m1 = vfma(two, diag, vfma(V::all(T(-4)), f[0], -axis));
+    V m2 = vfma(four, f[0], vfma(V::all(T(-2)), axis, diag));
+    if constexpr (SH) {
+        m1 = vfma(V::all(T(-2)), rs, m1);
+        m2 = m2 + rs;
+    }
     const V m4 = vfma(V::all(T(-2)), d13, d57 - d68);
     const V m6 = vfma(V::all(T(-2)), d24, d57 + d68);
     const V m7 = ax - ay;
@@ -362,9 +376,9 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
 
     // Eq. 17, written as (1 - s) m + s m_eq + (1 - s/2) S + C
     const V ms0 = rho;
-    const V ms1 = vfma(V::all(P.e_keep), m1, vfma(V::all(P.s_e), meq1,
+    V ms1 = vfma(V::all(P.e_keep), m1, vfma(V::all(P.s_e), meq1,
                   vfma(V::all(P.e_half), S1, V::all(P.e_src) * tr)));
-    const V ms2 = vfma(V::all(P.z_keep), m2, vfma(V::all(P.s_z), meq2,
+    V ms2 = vfma(V::all(P.z_keep), m2, vfma(V::all(P.s_z), meq2,
                   -vfma(V::all(P.z_half), S1, V::all(P.z_src) * tr)));
     const V ms3 = jx + Fx;
     const V ms4 = vfma(V::all(P.q_keep), m4, -vfma(V::all(P.s_q), rvx, V::all(P.q_half) * Fx));
@@ -383,9 +397,13 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     const V ms8 = vfma(vkeep, m8, vfma(vs, meq8, vfma(vhalf, S8, vsrc * Qxy)));
 
     // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    if constexpr (SH) {   // back to the moments of the shifted f*
+        ms1 = vfma(two, rs, ms1);
+        ms2 = ms2 - rs;
+    }
     const V c9 = V::all(T(1.0 / 9.0)), c18 = V::all(T(1.0 / 18.0)), c36 = V::all(T(1.0 / 36.0));
     const V c6 = V::all(T(1.0 / 6.0)), c12 = V::all(T(1.0 / 12.0)), c4 = V::all(T(0.25));
-    const V a0 = c9 * ms0;
+    const V a0 = c9 * (SH ? rsum : ms0);
     const V base_axis = a0 - vfma(c36, ms1, c18 * ms2);
     const V base_diag = vfma(c18, ms1, vfma(c36, ms2, a0));
     const V jx6 = c6 * ms3, qx6 = c6 * ms4, jy6 = c6 * ms5, qy6 = c6 * ms6;
@@ -405,7 +423,7 @@ __device__ __forceinline__ void collide_pair(V2<T> (&f)[9], const V2<T> (&pn)[9]
     // with the rounded constants 1/9, 1/18, 1/36 the column sums of M^-1 are not exactly
     // (1, 0, ..., 0), which in FP32 adds mass at about 7e-9 per step; this way the only
     // error is one unbiased rounding.
-    f[0] = rho - (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+    f[0] = rsum - (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
 }
 
 }  // namespace lbm

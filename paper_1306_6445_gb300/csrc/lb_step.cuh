@@ -237,15 +237,45 @@ __device__ __forceinline__ V2<T> lds_pair(const T *p) {
     return V2<T>(v.x, v.y);
 }
 
-// an aligned pair of stored elements from shared memory, decoded (population a)
+// The step kernels work on the stored values themselves: for LB_BF16 the shifted
+// f_a - w_a rho_s (exactly, as FP32), which the collision corrects in moment space
+// (collide_pair with SH), so neither the loads nor the stores apply the shift.
 template <typename T>
-__device__ __forceinline__ V2<Arith<T>> ring_pair(const T *p, int a,
-                                                  const DevConsts<Arith<T>> &P) {
+__device__ __forceinline__ Arith<T> stored_val(T v) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(v);
+    else return v;
+}
+
+// an aligned pair of stored elements from shared memory, as stored values
+template <typename T>
+__device__ __forceinline__ V2<Arith<T>> ring_pair(const T *p) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-        return V2<float>(v) + V2<float>::all(P.wshift[a]);   // lane-wise as pop_dec
+        return V2<float>(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p)));
     } else {
         return lds_pair<T>(p);
+    }
+}
+
+// the density of two sites from their stored values (plus rho_s for LB_BF16)
+template <typename T>
+__device__ __forceinline__ V2<Arith<T>> site_rho(const V2<Arith<T>> (&f)[9],
+                                                 const DevConsts<Arith<T>> &P) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        return rho_pair(f) + V2<float>::all(P.rho_s);
+    else
+        return rho_pair(f);
+}
+
+// a stored value from the value of the shifted population (LB_BF16; nearest or, SR,
+// stochastic rounding with the 16 random bits r16), the value itself otherwise
+template <typename T, bool SR>
+__device__ __forceinline__ T stored_enc(Arith<T> v, unsigned r16) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        if constexpr (SR) return bf16_stochastic(v, r16);
+        else return __float2bfloat16_rn(v);
+    } else {
+        (void)r16;
+        return v;
     }
 }
 
@@ -262,8 +292,8 @@ __device__ __forceinline__ void pull2(V2<Arith<T>> (&f)[9], const Ring<T> &r, in
     // stored population a sits in ring plane plane_of(a)
     auto two = [&](const T *row, int a, int dc) -> V2<A> {
         const T *pl = row + plane_of(a) * BW;
-        if (ADJ && dc == 0) return ring_pair<T>(pl + cA, a, P);
-        return V2<A>(pop_dec<T>(pl[cA + dc], a, P), pop_dec<T>(pl[cB + dc], a, P));
+        if (ADJ && dc == 0) return ring_pair<T>(pl + cA);
+        return V2<A>(stored_val<T>(pl[cA + dc]), stored_val<T>(pl[cB + dc]));
     };
     f[0] = two(r.z, 0, 0);
     f[1] = two(r.z, 1, -1);
@@ -305,14 +335,15 @@ __device__ __forceinline__ void store_pair<double>(double *p, V2<double> v, bool
     else p[0] = v.x;
 }
 
-// stored pair of population a (encoded from its value); SR: LB_BF16 with stochastic
+// stored pair from the pair of (shifted, for LB_BF16) values; SR: LB_BF16 with stochastic
 // rounding, r32 its random bits for the pair (low half for the first site, high half for
 // the second)
 template <typename T, bool SR = false>
 __device__ __forceinline__ void store_pop_pair(T *p, V2<Arith<T>> v, bool both, int a,
                                                const DevConsts<Arith<T>> &P, unsigned r32 = 0) {
+    (void)a; (void)P;
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        const V2<float> d = v - V2<float>::all(P.wshift[a]);   // lane-wise as pop_enc
+        const V2<float> d = v;
         if constexpr (SR) {
             const __nv_bfloat16 lo = bf16_stochastic(d.lo(), r32), hi = bf16_stochastic(d.hi(), r32 >> 16);
             if (both) *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(lo, hi);
@@ -438,7 +469,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
         const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
         if (act) {
             pull2<T, BC, BW, true>(keep, r, c0 + L, c0 + L + 1, bottom, top, P);
-            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
+            const V2<A> psi = eos_psi2<A, EOS>(site_rho<T>(keep, P), P, both, bad);
             if (both) {
                 store_pair<A>(ps + c0 + 2, psi, true);
             } else {
@@ -453,7 +484,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
                 if (x0 + w == nx) hb = w + L - 1;
             }
             pull2<T, BC, BW, false>(h, r, ha, hb, bottom, top, P);
-            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
+            const V2<A> psi = eos_psi2<A, EOS>(site_rho<T>(h, P), P, true, bad);
             ps[1] = psi.lo();
             ps[w + 2] = psi.hi();
         }
@@ -514,7 +545,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
             pn[6] = V2<A>(qL, q0.lo());
             pn[7] = V2<A>(mL, m0.lo());
             pn[8] = V2<A>(m0.hi(), mR);
-            collide_pair<A, BC == 2>(fc, pn, P);
+            collide_pair<A, BC == 2, std::is_same<T, __nv_bfloat16>::value>(fc, pn, P);
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)yr * (unsigned)pitch + (unsigned)(x + GH<T>);
@@ -530,7 +561,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
                         const unsigned r = store_bits<T, SR>(key, a, P);
-                        const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
+                        const T v0 = stored_enc<T, SR>(fc[a].lo(), r), v1 = stored_enc<T, SR>(fc[a].hi(), r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -543,7 +574,7 @@ __device__ __forceinline__ int march(const CUtensorMap *tmap, T *__restrict__ go
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const unsigned r = store_bits<T, SR>(key, a, P);
-                    const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
+                    const T v0 = stored_enc<T, SR>(fc[a].lo(), r), v1 = stored_enc<T, SR>(fc[a].hi(), r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
@@ -618,8 +649,8 @@ __device__ __forceinline__ void pull_stage(V2<Arith<T>> (&f)[9], const T *stg, i
     using A = Arith<T>;
     auto two = [&](int a, int dc) -> V2<A> {
         const T *pl = stg + (plane_of(a) / 3) * GS + (plane_of(a) % 3) * BW;
-        if (ADJ && dc == 0) return ring_pair<T>(pl + cA, a, P);
-        return V2<A>(pop_dec<T>(pl[cA + dc], a, P), pop_dec<T>(pl[cB + dc], a, P));
+        if (ADJ && dc == 0) return ring_pair<T>(pl + cA);
+        return V2<A>(stored_val<T>(pl[cA + dc]), stored_val<T>(pl[cB + dc]));
     };
     f[0] = two(0, 0);
     f[1] = two(1, -1);
@@ -724,7 +755,7 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
         const bool bottom = WALLS && Y == 0, top = WALLS && Y == ny - 1;
         if (act) {
             pull_stage<T, BC, BW, GS, true>(keep, stg, c0 + L, c0 + L + 1, bottom, top, P);
-            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(keep), P, both, bad);
+            const V2<A> psi = eos_psi2<A, EOS>(site_rho<T>(keep, P), P, both, bad);
             if (both) {
                 store_pair<A>(ps + c0 + 2, psi, true);
             } else {
@@ -739,7 +770,7 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
                 if (x0 + w == nx) hb = w + L - 1;
             }
             pull_stage<T, BC, BW, GS, false>(h, stg, ha, hb, bottom, top, P);
-            const V2<A> psi = eos_psi2<A, EOS>(rho_pair(h), P, true, bad);
+            const V2<A> psi = eos_psi2<A, EOS>(site_rho<T>(h, P), P, true, bad);
             ps[1] = psi.lo();
             ps[w + 2] = psi.hi();
         }
@@ -793,7 +824,7 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
             pn[6] = V2<A>(qL, q0.lo());
             pn[7] = V2<A>(mL, m0.lo());
             pn[8] = V2<A>(m0.hi(), mR);
-            collide_pair<A, BC == 2>(fc, pn, P);
+            collide_pair<A, BC == 2, std::is_same<T, __nv_bfloat16>::value>(fc, pn, P);
 
             const int x = x0 + c0;
             const unsigned idx = (unsigned)y * (unsigned)pitch + (unsigned)(x + GH<T>);
@@ -815,7 +846,7 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
 #pragma unroll
                     for (int a = 0; a < 9; ++a) {
                         const unsigned r = store_bits<T, SR>(key, a, P);
-                        const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
+                        const T v0 = stored_enc<T, SR>(fc[a].lo(), r), v1 = stored_enc<T, SR>(fc[a].hi(), r >> 16);
                         T *rb = gout + (rowi + plane_of(a) * plane);
                         if (x == 0) rb[GH<T> - 1] = rb[GH<T> - 2] = v0;
                         if (x == nx - 1) rb[nx + GH<T>] = rb[nx + GH<T> + 1] = v0;
@@ -827,7 +858,7 @@ __device__ __forceinline__ int march_stage(const CUtensorMap *tmap, T *__restric
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const unsigned r = store_bits<T, SR>(key, a, P);
-                    const T v0 = pop_enc<T, SR>(fc[a].lo(), a, P, r), v1 = pop_enc<T, SR>(fc[a].hi(), a, P, r >> 16);
+                    const T v0 = stored_enc<T, SR>(fc[a].lo(), r), v1 = stored_enc<T, SR>(fc[a].hi(), r >> 16);
                     T *rb = gout + (rowi + plane_of(a) * plane);
                     if (x < 2) rb[nx + GH<T> + x] = v0;
                     if (both && x + 1 < 2) rb[nx + GH<T> + x + 1] = v1;
