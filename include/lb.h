@@ -56,10 +56,11 @@ typedef enum {
 typedef enum { LB_EOS_CS = 0, LB_EOS_EXP = 1, LB_EOS_PIECEWISE = 2 } lb_eos_kind;
 /* Storage / arithmetic precision of a context's populations:
  *  LB_FP64, LB_FP32: stored and computed in that type;
- *  LB_BF16: stored as BF16 (round to nearest even) of the FP32 difference f_a - w_a rho_s,
- *           w = 4/9, 1/9 (a = 1..4), 1/36 (a = 5..8), rho_s set by lb_set_storage_shift
- *           (default 0); every step decodes f_a = float(stored) + w_a rho_s and computes in
- *           FP32. Single contexts only (not batches). */
+ *  LB_BF16: stored as BF16 (round to nearest even, or stochastically) of the shifted
+ *           population f_a - w_a rho_s, w = 4/9, 1/9 (a = 1..4), 1/36 (a = 5..8), rho_s set
+ *           by lb_set_storage_shift (default 0); a step computes in FP32 on the shifted
+ *           values (the shift enters the moments rho, e and zeta), and f_a = float(stored)
+ *           + w_a rho_s everywhere else. Single contexts only (not batches). */
 typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_BF16 = 2 } lb_prec;
 /* Boundaries: LB_BC_PERIODIC in x and y; LB_BC_WALLS_Y periodic in x with half-way
  * bounce-back (no-slip) walls below row 0 and above row ny-1 (Sec. V.B); LB_BC_OPEN a
