@@ -40,6 +40,27 @@ def test_m_matches_polynomial_rows_of_the_twin():
     assert np.array_equal(L.M, BF.M_BF.astype(np.float64))
 
 
+def test_storage_shift_moves_only_the_rho_e_zeta_moments():
+    """The LB_BF16 step works on the stored shifted populations g = f - w rho_s: since
+    M w = (1, -2, 1, 0, ..., 0), the moments of f are those of g plus rho_s (1, -2, 1) in
+    rho, e and zeta, and M^-1 of m* less the same gives the shifted post-collision
+    populations; f*_0 from mass conservation reads the same in shifted terms."""
+    w36 = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1], dtype=np.float64)      # 36 w, exact
+    assert np.array_equal(L.M @ w36, np.array([36, -72, 36, 0, 0, 0, 0, 0, 0]))
+    rng = np.random.default_rng(11)
+    g = rng.normal(0.0, 0.05, size=9)
+    rho_s = 0.37
+    shift = np.array([1.0, -2.0, 1.0, 0, 0, 0, 0, 0, 0]) * rho_s
+    assert np.allclose(L.M @ (g + W_EQ * rho_s), L.M @ g + shift, rtol=0, atol=1e-15)
+    m_star = rng.normal(0.0, 0.1, size=9)
+    f_star = L.M_INV @ m_star
+    assert np.allclose(L.M_INV @ (m_star - shift), f_star - W_EQ * rho_s, rtol=0, atol=1e-15)
+    rho = np.sum(g) + rho_s
+    f0 = rho - np.sum(f_star[1:])                        # mass conservation, plain
+    g0 = np.sum(g) - np.sum(f_star[1:] - W_EQ[1:] * rho_s)   # the same, shifted
+    assert g0 == pytest.approx(f0 - W_EQ[0] * rho_s, abs=1e-14)
+
+
 def test_equilibrium_moments_equal_m_times_textbook_feq():
     """Eq. 3 is M applied to the textbook D2Q9 equilibrium (checks every row of M and Eq. 3)."""
     rng = np.random.default_rng(3)
