@@ -37,3 +37,19 @@ def window(f, x, y, walls_y, half=2):
 def rel_err(a, b):
     return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max()
                  / np.abs(np.asarray(b, np.float64)).max())
+
+
+def zero_crossings(ts, ys, half=2000.0):
+    """Times where ys changes sign, each from a least-squares line through the samples
+    within `half` steps of the sign change (the mode amplitude carries small acoustic
+    ripples); sign changes closer than 2 half to the previous one count once."""
+    out = []
+    for i in range(len(ys) - 1):
+        if ys[i] * ys[i + 1] < 0:
+            tc = 0.5 * (ts[i] + ts[i + 1])
+            if out and tc - out[-1] < 2.0 * half:
+                continue
+            s = np.abs(ts - tc) <= half
+            b, a = np.polyfit(ts[s] - tc, ys[s], 1)
+            out.append(tc - a / b)
+    return out

@@ -29,7 +29,7 @@ from oracle import diagnostics as D
 from oracle import eos as OE
 from paper_1306_6445_gb300 import inputs as I
 
-from _util import oracle_params
+from _util import oracle_params, zero_crossings
 
 pytestmark = pytest.mark.gpu
 
@@ -135,22 +135,6 @@ def test_2048_droplet_converged_surface_tension_fp32_and_fp64(lbm):
     assert ra32 == pytest.approx(ra64, rel=5e-3)
 
 
-def _zero_crossings(ts, ys, half=2000.0):
-    """Times where ys changes sign, each from a least-squares line through the samples
-    within `half` steps of the sign change (the mode amplitude carries small acoustic
-    ripples); sign changes closer than 2 half to the previous one count once."""
-    out = []
-    for i in range(len(ys) - 1):
-        if ys[i] * ys[i + 1] < 0:
-            tc = 0.5 * (ts[i] + ts[i + 1])
-            if out and tc - out[-1] < 2.0 * half:
-                continue
-            s = np.abs(ts - tc) <= half
-            b, a = np.polyfit(ts[s] - tc, ys[s], 1)
-            out.append(tc - a / b)
-    return out
-
-
 # steps to the first two zero crossings of the mode (the second only where it is timed)
 _CAP_STEPS = {(4, 0.0): 90000, (4, 0.5): 130000, (2, 0.0): 260000, (2, 0.5): 365000,
               (1, 0.0): 265000, (1, 0.5): 370000}
@@ -185,7 +169,7 @@ def test_4096x2048_capillary_wave_frequency_follows_the_dispersion_relation(lbm,
             lat.step(500)
         lat.close()
         ts, amp = np.array(ts, float), np.array(amp)
-        z = _zero_crossings(ts, amp)
+        z = zero_crossings(ts, amp)
         assert abs(amp[0] - 0.01 * lam) < 1.0
         print(f"k {k}, kappa {kappa}: mode amplitude every 10000 steps {np.round(amp[::20], 2)}")
         if k == 1:

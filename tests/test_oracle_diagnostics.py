@@ -115,3 +115,18 @@ def test_laplace_fit_of_step_droplets_has_no_slope():
     jump = float(E.p_eos(rho_l, eos, -1.0) - E.p_eos(rho_v, eos, -1.0))
     assert abs(t) < 1e-12 * abs(jump) * 40
     assert c == pytest.approx(jump, rel=1e-12)
+
+
+def test_zero_crossings_of_a_rippled_damped_cosine():
+    """The crossing finder of the capillary-wave test: a damped cosine sampled every 500
+    steps with a small fast ripple gives its zero crossings (pi/2 + k pi)/omega to within a
+    few steps, each sign change counted once."""
+    from _util import zero_crossings
+    omega = 2 * np.pi / 110000.0
+    ts = np.arange(0, 130001, 500, dtype=float)
+    ys = 10.0 * np.exp(-7e-6 * ts) * np.cos(omega * ts) + 0.05 * np.sin(2 * np.pi * ts / 3500.0)
+    z = zero_crossings(ts, ys)
+    exact = [(np.pi / 2 + k * np.pi) / omega for k in range(2)]
+    assert len(z) == 2
+    assert np.allclose(z, exact, atol=100.0)
+    assert np.pi / (z[1] - z[0]) == pytest.approx(omega, rel=2e-3)
